@@ -1,0 +1,340 @@
+"""Seeded synthetic inputs for the VLBM step: initial fields W0, objective weights, directions.
+
+This module only builds inputs.  It contains none of the time step's arithmetic (no
+equilibrium, flux, sensor, relaxation or streaming); the one piece of thermodynamics here is the
+conversion of a primitive state (rho, u, v, P) into the conserved vector
+W = (rho, rho u, rho v, rho E) of Sec. II A (Eqs. 1-2), which is how every initial condition of
+the paper is stated.
+
+Random numbers come from splitmix64 (Steele, Lea & Flood 2014) mapped to 53-bit doubles, so the
+same seed gives the same fields on every platform.  Field arrays are float64, shaped
+(D+2, ny, nx) with x fastest (1D problems have ny = 1).  Cell centres are x_j = x0 + (j + 1/2) dx.
+"""
+from __future__ import annotations
+
+import dataclasses
+import json
+import math
+import os
+from typing import Callable, Optional, Sequence
+
+import numpy as np
+
+_MASK64 = (1 << 64) - 1
+
+
+class SplitMix64:
+    """splitmix64 stream: state += 0x9E3779B97F4A7C15, then the published mix of the state."""
+
+    def __init__(self, seed: int):
+        self.state = seed & _MASK64
+
+    def next_u64(self) -> int:
+        self.state = (self.state + 0x9E3779B97F4A7C15) & _MASK64
+        z = self.state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _MASK64
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _MASK64
+        return z ^ (z >> 31)
+
+    def uniform(self, lo: float = 0.0, hi: float = 1.0) -> float:
+        """Uniform double in [lo, hi) from the top 53 bits."""
+        return lo + (hi - lo) * ((self.next_u64() >> 11) * (1.0 / (1 << 53)))
+
+    def integer(self, lo: int, hi: int) -> int:
+        """Integer in [lo, hi] (inclusive)."""
+        return lo + min(int(self.uniform() * (hi - lo + 1)), hi - lo)
+
+
+# ------------------------------------------------------------------------------------------
+# Problem descriptions (plain data).
+# ------------------------------------------------------------------------------------------
+@dataclasses.dataclass(frozen=True)
+class Problem:
+    name: str
+    dim: int
+    nx: int
+    ny: int
+    extent: tuple  # (x0, x1, y0, y1)
+    bc: tuple  # (x-lo, x-hi, y-lo, y-hi): "periodic" | "zerograd"
+    eos: dict  # {"kind": "ideal", "gamma": g} | {"kind": "vdw", "a", "b", "R", "cv"}
+    cfl: float
+    t_end: float  # 0: run a fixed number of steps
+    n_steps: int  # steps of a full run (0: run to t_end)
+    beta_min: float = 0.75
+    beta_max: float = 1.0
+    c_sensor: float = 4.0
+    ducros_eps: float = 1e-12
+
+    @property
+    def dx(self) -> float:
+        return (self.extent[1] - self.extent[0]) / self.nx
+
+    @property
+    def ncells(self) -> int:
+        return self.nx * self.ny
+
+    def resized(self, nx: int, ny: Optional[int] = None) -> "Problem":
+        return dataclasses.replace(self, nx=nx, ny=(1 if self.dim == 1 else (ny if ny is not None else nx)))
+
+
+IDEAL14 = {"kind": "ideal", "gamma": 1.4}
+# Reduced van der Waals units (rho_c = P_c = T_c = 1): a = 3, b = 1/3, R = 8/3, cv = 50 R.
+VDW_REDUCED = {"kind": "vdw", "a": 3.0, "b": 1.0 / 3.0, "R": 8.0 / 3.0, "cv": 50.0 * 8.0 / 3.0}
+
+ZG = ("zerograd",) * 4
+PER = ("periodic",) * 4
+
+SOD_1D = Problem("sod_1d_1000", 1, 1000, 1, (0.0, 1.0, 0.0, 0.0), ZG, IDEAL14, 0.5, 0.2, 0)
+QUADRANTS_2D = Problem("quadrants_2d_4096", 2, 4096, 4096, (0.0, 1.0, 0.0, 1.0), ZG, IDEAL14, 0.5, 0.25, 0)
+BZT_2D = Problem("bzt_interface_2d_2048", 2, 2048, 2048, (0.0, 1.0, 0.0, 1.0), ZG, VDW_REDUCED, 0.5, 0.2, 0)
+VORTEX_SCALE_2D = Problem("vortex_acoustic_2d_8192", 2, 8192, 8192, (0.0, 10.0, 0.0, 10.0), PER, IDEAL14, 0.5, 0.0, 2000)
+VORTEX_ADJOINT_2D = Problem("vortex_adjoint_2d_1024", 2, 1024, 1024, (0.0, 10.0, 0.0, 10.0), PER, IDEAL14, 0.5, 0.0, 1000)
+
+PROBLEMS = {p.name: p for p in (SOD_1D, QUADRANTS_2D, BZT_2D, VORTEX_SCALE_2D, VORTEX_ADJOINT_2D)}
+
+
+def cell_centres(p: Problem):
+    x0, x1, y0, y1 = p.extent
+    dx = p.dx
+    x = x0 + (np.arange(p.nx) + 0.5) * dx
+    if p.dim == 1:
+        return x[None, :], np.zeros((1, p.nx))
+    y = y0 + (np.arange(p.ny) + 0.5) * dx
+    X, Y = np.meshgrid(x, y, indexing="xy")
+    return X, Y
+
+
+# ------------------------------------------------------------------------------------------
+# Primitive -> conserved (Sec. II A, Eqs. 1-2) with the internal energy of the closure
+# (Eq. 15 ideal gas; Eqs. 16-17 van der Waals solved for T, then e = cv T - a rho).
+# ------------------------------------------------------------------------------------------
+def internal_energy(eos: dict, rho, P):
+    if eos["kind"] == "ideal":
+        return P / ((eos["gamma"] - 1.0) * rho)
+    a, b, R, cv = eos["a"], eos["b"], eos["R"], eos["cv"]
+    T = (P + a * rho * rho) * (1.0 - b * rho) / (R * rho)
+    return cv * T - a * rho
+
+
+def vdw_pressure_at_T(eos: dict, rho, T):
+    a, b, R = eos["a"], eos["b"], eos["R"]
+    return R * rho * T / (1.0 - b * rho) - a * rho * rho
+
+
+def vdw_temperature(eos: dict, rho, P):
+    a, b, R = eos["a"], eos["b"], eos["R"]
+    return (P + a * rho * rho) * (1.0 - b * rho) / (R * rho)
+
+
+def conserved(eos: dict, rho, vel: Sequence, P) -> np.ndarray:
+    rho = np.asarray(rho, dtype=np.float64)
+    vel = [np.asarray(v, dtype=np.float64) for v in vel]
+    e = internal_energy(eos, rho, np.asarray(P, dtype=np.float64))
+    ke = 0.5 * sum(v * v for v in vel)
+    comps = [rho] + [rho * v for v in vel] + [rho * (e + ke)]
+    return np.ascontiguousarray(np.stack([np.broadcast_to(c, rho.shape) for c in comps]).astype(np.float64))
+
+
+# ------------------------------------------------------------------------------------------
+# Initial conditions
+# ------------------------------------------------------------------------------------------
+def sod_1d(p: Problem = SOD_1D, left=(1.0, 0.0, 1.0), right=(0.125, 0.0, 0.1), x_interface=0.5) -> np.ndarray:
+    """Two-state 1D Riemann problem: (rho, u, P) left / right of x_interface."""
+    X, _ = cell_centres(p)
+    L = X < x_interface
+    rho = np.where(L, left[0], right[0])
+    u = np.where(L, left[1], right[1])
+    P = np.where(L, left[2], right[2])
+    return conserved(p.eos, rho, [u], P)
+
+
+def quadrant_states(seed: int = 2):
+    """Four (rho, u, v, P) states in NE, NW, SW, SE order; per state rho~U[0.1,2], u,v~U[-1,1],
+    P~U[0.05,2], drawn in that order."""
+    g = SplitMix64(seed)
+    out = []
+    for _ in range(4):
+        rho = g.uniform(0.1, 2.0)
+        u = g.uniform(-1.0, 1.0)
+        v = g.uniform(-1.0, 1.0)
+        P = g.uniform(0.05, 2.0)
+        out.append((rho, u, v, P))
+    return out
+
+
+def quadrants_2d(p: Problem = QUADRANTS_2D, seed: int = 2, states=None) -> np.ndarray:
+    """Four-quadrant 2D Riemann problem with the discontinuities on x = 0.5 and y = 0.5."""
+    st = states if states is not None else quadrant_states(seed)
+    X, Y = cell_centres(p)
+    xm = 0.5 * (p.extent[0] + p.extent[1])
+    ym = 0.5 * (p.extent[2] + p.extent[3])
+    E, N = X >= xm, Y >= ym
+    masks = [E & N, ~E & N, ~E & ~N, E & ~N]  # NE, NW, SW, SE
+    fields = [np.zeros(X.shape) for _ in range(4)]
+    for m, s in zip(masks, st):
+        for j in range(4):
+            fields[j][m] = s[j]
+    rho, u, v, P = fields
+    return conserved(p.eos, rho, [u, v], P)
+
+
+def draw_bzt_candidates(seed: int, count: int):
+    """Candidate left/right (rho, P) pairs in [0.4, 0.95] x [0.8, 1.15], drawn rho then P."""
+    g = SplitMix64(seed)
+    return [(g.uniform(0.4, 0.95), g.uniform(0.8, 1.15)) for _ in range(count)]
+
+
+_BZT_STATES_FILE = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "tests", "golden",
+                                "bzt_states_seed3.json")
+
+
+def bzt_states(seed: int = 3, accept: Optional[Callable[[float, float], bool]] = None):
+    """Left and right (rho, P) states of the BZT interface problem: the first two candidates of
+    the seed's stream accepted by `accept` (c_s^2 > 0 and fundamental derivative Gamma < 0).
+    Without a predicate, the states stored for seed 3 (written by the fixture script beside the
+    file, from the oracle's EOS) are returned."""
+    if accept is None:
+        with open(_BZT_STATES_FILE) as fh:
+            d = json.load(fh)
+        if d["seed"] != seed:
+            raise ValueError(f"stored BZT states are for seed {d['seed']}, not {seed}")
+        return [tuple(d["left"]), tuple(d["right"])]
+    out = []
+    for rho, P in draw_bzt_candidates(seed, 10000):
+        if accept(rho, P):
+            out.append((rho, P))
+            if len(out) == 2:
+                return out
+    raise RuntimeError("no two accepted BZT states in 10000 draws")
+
+
+def bzt_interface_2d(p: Problem = BZT_2D, seed: int = 3, states=None, amp: float = 1e-3, modes: int = 16) -> np.ndarray:
+    """Planar interface at x = 0.5 between two van der Waals states at rest, with the density
+    multiplied by 1 + amp * mean_m cos(2 pi (n_x x + n_y y) + phi_m) at fixed temperature;
+    n_x, n_y ~ integers in [1, 8], phi ~ U[0, 2 pi), drawn from seed + 1000."""
+    (rl, Pl), (rr, Pr) = states if states is not None else bzt_states(seed)
+    X, Y = cell_centres(p)
+    L = X < 0.5 * (p.extent[0] + p.extent[1])
+    rho0 = np.where(L, rl, rr)
+    T = np.where(L, vdw_temperature(p.eos, rl, Pl), vdw_temperature(p.eos, rr, Pr))
+    g = SplitMix64(seed + 1000)
+    pert = np.zeros(X.shape)
+    for _ in range(modes):
+        nx_, ny_ = g.integer(1, 8), g.integer(1, 8)
+        phi = g.uniform(0.0, 2.0 * math.pi)
+        pert += np.cos(2.0 * math.pi * (nx_ * X + ny_ * Y) + phi)
+    rho = rho0 * (1.0 + amp * pert / modes)
+    P = vdw_pressure_at_T(p.eos, rho, T)
+    z = np.zeros(X.shape)
+    return conserved(p.eos, rho, [z, z], P)
+
+
+def _modes(g: SplitMix64, count: int, nmax: int):
+    out = []
+    while len(out) < count:
+        nx_, ny_ = g.integer(-nmax, nmax), g.integer(-nmax, nmax)
+        if nx_ == 0 and ny_ == 0:
+            continue
+        out.append((nx_, ny_, g.uniform(0.0, 2.0 * math.pi)))
+    return out
+
+
+def vortex_primitives(p: Problem, strength: float = 5.0, background=(1.0, 0.5, 0.5, 1.0), centre=None):
+    """Ideal-gas isentropic (Yee/Shu) vortex of core radius 1 on a uniform background
+    (rho, u, v, P); temperature T = P/rho:
+      T = T_inf - (gamma-1) s^2 / (8 gamma pi^2) exp(1 - r^2),
+      (du, dv) = s / (2 pi) exp((1 - r^2)/2) (-(y - yc), x - xc),
+      rho = rho_inf (T/T_inf)^(1/(gamma-1)), P = rho T."""
+    gam = p.eos["gamma"]
+    X, Y = cell_centres(p)
+    if centre is None:
+        centre = (0.5 * (p.extent[0] + p.extent[1]), 0.5 * (p.extent[2] + p.extent[3]))
+    rho_inf, u_inf, v_inf, P_inf = background
+    T_inf = P_inf / rho_inf
+    dx_, dy_ = X - centre[0], Y - centre[1]
+    r2 = dx_ * dx_ + dy_ * dy_
+    T = T_inf - (gam - 1.0) * strength ** 2 / (8.0 * gam * math.pi ** 2) * np.exp(1.0 - r2)
+    rho = rho_inf * (T / T_inf) ** (1.0 / (gam - 1.0))
+    amp = strength / (2.0 * math.pi) * np.exp(0.5 * (1.0 - r2))
+    u = u_inf - amp * dy_
+    v = v_inf + amp * dx_
+    return rho, u, v, rho * T
+
+
+def vortex_acoustic_2d(p: Problem = VORTEX_SCALE_2D, seed: int = 4, amp: float = 1e-3, waves: int = 8) -> np.ndarray:
+    """Isentropic vortex plus `waves` seeded acoustic plane waves with integer modes
+    |n_x|, |n_y| <= 8: dP = amp P_inf cos(2 pi n.x / L + phi) / waves, drho = dP / c_inf^2,
+    du = dP / (rho_inf c_inf) n/|n|."""
+    rho, u, v, P = vortex_primitives(p)
+    gam = p.eos["gamma"]
+    rho_inf, P_inf = 1.0, 1.0
+    c_inf = math.sqrt(gam * P_inf / rho_inf)
+    X, Y = cell_centres(p)
+    L = p.extent[1] - p.extent[0]
+    g = SplitMix64(seed)
+    for nx_, ny_, phi in _modes(g, waves, 8):
+        dP = amp * P_inf * np.cos(2.0 * math.pi * (nx_ * X + ny_ * Y) / L + phi) / waves
+        nn = math.hypot(nx_, ny_)
+        P = P + dP
+        rho = rho + dP / c_inf ** 2
+        u = u + dP / (rho_inf * c_inf) * nx_ / nn
+        v = v + dP / (rho_inf * c_inf) * ny_ / nn
+    return conserved(p.eos, rho, [u, v], P)
+
+
+def vortex_density_2d(p: Problem = VORTEX_ADJOINT_2D, seed: int = 5, amp: float = 1e-2, modes: int = 8) -> np.ndarray:
+    """Isentropic vortex with the density multiplied by 1 + amp * mean_m cos(2 pi n.x / L + phi_m)
+    at fixed pressure, integer modes |n_x|, |n_y| <= 8."""
+    rho, u, v, P = vortex_primitives(p)
+    X, Y = cell_centres(p)
+    L = p.extent[1] - p.extent[0]
+    g = SplitMix64(seed)
+    pert = np.zeros(X.shape)
+    for nx_, ny_, phi in _modes(g, modes, 8):
+        pert += np.cos(2.0 * math.pi * (nx_ * X + ny_ * Y) / L + phi)
+    rho = rho * (1.0 + amp * pert / modes)
+    return conserved(p.eos, rho, [u, v], P)
+
+
+def objective_weight(p: Problem = VORTEX_ADJOINT_2D, seed: int = 50, modes: int = 4) -> np.ndarray:
+    """Smooth weight g(x) = 1 + 1/2 mean_m cos(2 pi n.x / L + phi_m), |n_x|, |n_y| <= 3; shape (ny, nx)."""
+    X, Y = cell_centres(p)
+    L = p.extent[1] - p.extent[0]
+    g = SplitMix64(seed)
+    acc = np.zeros(X.shape)
+    for nx_, ny_, phi in _modes(g, modes, 3):
+        acc += np.cos(2.0 * math.pi * (nx_ * X + ny_ * Y) / L + phi)
+    return np.ascontiguousarray(1.0 + 0.5 * acc / modes)
+
+
+def directions(p: Problem, count: int = 20, seed: int = 500, modes: int = 4) -> np.ndarray:
+    """`count` smooth perturbation fields of the initial W, each a sum of `modes` seeded Fourier
+    modes (|n_x|, |n_y| <= 4) per component, scaled to unit RMS over all components and cells;
+    shape (count, D+2, ny, nx)."""
+    X, Y = cell_centres(p)
+    L = p.extent[1] - p.extent[0]
+    nc = p.dim + 2
+    g = SplitMix64(seed)
+    out = np.zeros((count, nc) + X.shape)
+    for d in range(count):
+        for k in range(nc):
+            for nx_, ny_, phi in _modes(g, modes, 4):
+                out[d, k] += np.cos(2.0 * math.pi * (nx_ * X + ny_ * Y) / L + phi)
+        out[d] /= math.sqrt(np.mean(out[d] ** 2))
+    return out
+
+
+def initial_field(p: Problem) -> np.ndarray:
+    """W0 of a named problem at its (possibly resized) grid."""
+    base = p.name.split("@")[0]
+    if base.startswith("sod_1d"):
+        return sod_1d(p)
+    if base.startswith("quadrants_2d"):
+        return quadrants_2d(p)
+    if base.startswith("bzt_interface_2d"):
+        return bzt_interface_2d(p)
+    if base.startswith("vortex_acoustic_2d"):
+        return vortex_acoustic_2d(p)
+    if base.startswith("vortex_adjoint_2d"):
+        return vortex_density_2d(p)
+    raise KeyError(p.name)
