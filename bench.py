@@ -1,0 +1,368 @@
+#!/usr/bin/env python3
+"""Benchmark of the VLBM time step on one B300 (or N independent replicas, one per GPU).
+
+Workload: the 2D four-quadrant Riemann problem on 4096 x 4096 cells (ideal gas gamma 1.4,
+zero-gradient boundaries, CFL 0.5, shock sensor B), seeded synthetic input.  One benchmark
+"step" is one vlbm_step call advancing the solver by --substeps time steps (each time step
+runs the whole hot path: streaming, moments, EOS, flux, global maxima, link-speed update,
+reprojection, sensor, relaxation).  The populations (2.1 GB in FP64) exceed the 126 MB L2, so no
+flush is needed between steps.
+
+Reported: FP64 MLUPS (`value`), the FP32-storage variant, the dominant kernel's roofline with its
+live CUDA-event duration, the end-to-end number through the C ABI with host buffers, and the
+oracle timed on this host's cores.  `--impl reference` times the oracle alone.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--substeps S] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS & HBM-roofline fraction: FP64 vs FP32-store fwd; adjoint/fwd time, at stated error"
+UNIT = "MLUPS"
+# Algorithmic bytes per cell update: every population read once and written once
+# (2D: 4 directions x 4 components x 2).
+BYTES_PER_CELL = {"fp64": 256, "fp32_store": 128}
+# Algorithmic FP64 floating-point operations per 2D cell update (ideal gas, shock sensor) of the
+# fused step, FMA counted as 2, divide and square root as 1 each (count in the design notes).
+FP64_FLOPS_PER_CELL = 214
+SMS, FP64_FMA_PER_CLK_PER_SM = 148, 2
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return {"hbm_gbs": float(d["hbm_gbs"]), "sm_max_mhz": float(d.get("sm_max_mhz", 2032.0)), "source": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6400.0, "sm_max_mhz": 2032.0, "source": "fallback"}
+
+
+def fp64_peak_tflops(sm_mhz):
+    """Dense FP64 peak from unit counts and clock: 148 SMs x 2 FP64 FMA/clk x 2 flop x f_SM."""
+    return SMS * FP64_FMA_PER_CLK_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi samples of the SM clock and throttle reasons during a timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for j, n in enumerate(names):
+                    if r[5 + j].strip().lower() in ("active", "1"):
+                        reasons.add(n)
+            except Exception:
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_traffic(kind):
+    """DRAM bytes per cell of the dominant kernel from the committed ncu summary, or None when the
+    kernel source changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(path))
+        entry = d[kind]
+    except Exception:
+        return None
+    src = os.path.join(ROOT, "paper_2609_10639_b300", "csrc", "vlbm_kernels.cu")
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if entry.get("kernels_sha") != digest:
+        return None
+    return float(entry["dram_bytes_per_cell"])
+
+
+def dist_init():
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def time_path(prob, W0, precision, S, K, W, world, clocks_idx=None):
+    """Times K vlbm_step(S) calls on device-resident inputs after W untimed ones."""
+    import torch
+
+    from paper_2609_10639_b300 import vlbm
+
+    s = vlbm.Solver.for_problem(prob, precision=precision)
+    s.init(W0)
+    for _ in range(W):
+        s.step(S)
+    s.set_profiling(True)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(clocks_idx) if clocks_idx is not None else None
+    if sampler:
+        sampler.__enter__()
+    e0.record()
+    for _ in range(K):
+        done = s.step(S)
+        assert done == S
+    e1.record()
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.__exit__()
+    barrier(world)
+    ms = max_over_ranks(e0.elapsed_time(e1), world)
+    kms, launches = s.profile()
+    s.set_profiling(False)
+    lps = s.launches_per_step()
+    t, n, c = s.time()
+    s.close()
+    return {"ms": ms, "kernel_ms_avg": kms / max(launches, 1), "kernel_launches": launches, "launches_per_step": lps,
+            "t": t, "n": n, "clocks": sampler.summary() if sampler else None}
+
+
+def time_e2e(prob, W0_host, precision, S, K, world):
+    """Same metric through the C ABI with host buffers: each step uploads W0 from pinned host
+    memory (vlbm_init), advances S steps and reads W back into pinned host memory."""
+    import torch
+
+    from paper_2609_10639_b300 import vlbm
+
+    s = vlbm.Solver.for_problem(prob, precision=precision)
+    out = torch.empty(W0_host.shape, dtype=torch.float64).pin_memory()
+    s.init(W0_host)
+    s.step(S)
+    s.W(out=out)
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(K):
+        s.init(W0_host)
+        s.step(S)
+        s.W(out=out)
+    torch.cuda.synchronize()
+    dt = max_over_ranks(time.perf_counter() - t0, world)
+    s.close()
+    nbytes = W0_host.numel() * 8
+    return dt, nbytes
+
+
+def oracle_sample(min_seconds=10.0, n=1024, chunk=5, max_steps=None):
+    """The oracle (as it stands) on a bounded sample of the workload: the same input generator at
+    n x n cells, stepped in chunks until min_seconds of CPU work (or max_steps) have run."""
+    from oracle import oracle as O
+    from paper_2609_10639_b300 import workloads as wl
+
+    p = wl.QUADRANTS_2D.resized(n)
+    s = O.OracleSolver.for_problem(p)
+    s.init(wl.quadrants_2d(p))
+    steps, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < min_seconds and (max_steps is None or steps < max_steps):
+        steps += s.step(chunk)
+    dt = time.perf_counter() - t0
+    return {"value": p.ncells * steps / dt / 1e6, "unit": UNIT, "cores": s.threads, "kind": "oracle",
+            "sample": f"quadrants_2d seed input at {n}x{n}, {steps} FP64 steps from t=0, {dt:.1f} s of CPU work"}
+
+
+def run_reference(args):
+    """The reference arm: the oracle timed on the host cores, same metric and workload."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1 and rank != 0:
+        return
+    from paper_2609_10639_b300 import workloads as wl
+
+    for _ in range(args.warmup):
+        oracle_sample(min_seconds=0.0, max_steps=2, chunk=2)
+    vals, t0 = [], time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(oracle_sample(min_seconds=0.0, max_steps=4, chunk=4))
+    total = time.perf_counter() - t0
+    value = statistics.median(v["value"] for v in vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.QUADRANTS_2D.name, "sample": "1024x1024 copy of the input, 4 steps per step",
+                       "parallelism": "host cores (OpenMP)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": vals[0]["cores"], "kind": "oracle",
+                             "sample": vals[0]["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_only(args):
+    """One path on an n x n copy of the workload (profiling captures and sweeps)."""
+    import torch
+
+    from paper_2609_10639_b300 import workloads as wl
+
+    world, rank, local = dist_init()
+    prob = wl.QUADRANTS_2D.resized(args.grid) if args.grid else wl.QUADRANTS_2D
+    W0 = torch.from_numpy(wl.quadrants_2d(prob)).cuda()
+    r = time_path(prob, W0, args.only, args.substeps, args.steps, args.warmup, world)
+    if rank == 0:
+        mlups = world * prob.ncells * args.substeps * args.steps / (r["ms"] * 1e-3) / 1e6
+        kern_gbs = BYTES_PER_CELL[args.only] * prob.ncells / (r["kernel_ms_avg"] * 1e-3) / 1e9
+        print(json.dumps({"only": args.only, "workload": prob.name, "grid": [prob.nx, prob.ny], "value": mlups,
+                          "unit": UNIT, "ms_per_step": r["ms"] / args.steps, "kernel_ms": r["kernel_ms_avg"],
+                          "kernel_alg_gbs": kern_gbs, "t": r["t"], "n": r["n"]}), flush=True)
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2609_10639_b300 import vlbm, workloads as wl  # noqa: F401  (raises if the library is missing)
+
+    world, rank, local = dist_init()
+    prob = wl.QUADRANTS_2D
+    W0_np = wl.quadrants_2d(prob)
+    W0 = torch.from_numpy(W0_np).cuda()
+    S, K, Wm = args.substeps, args.steps, args.warmup
+    pk = peaks()
+    cells = prob.ncells
+
+    r64 = time_path(prob, W0, "fp64", S, K, Wm, world, clocks_idx=local)
+    mlups64 = world * cells * S * K / (r64["ms"] * 1e-3) / 1e6
+    r32 = time_path(prob, W0, "fp32_store", S, K, Wm, world)
+    mlups32 = world * cells * S * K / (r32["ms"] * 1e-3) / 1e6
+
+    W0_host = torch.from_numpy(W0_np).pin_memory()
+    dt_e2e, nbytes = time_e2e(prob, W0_host, "fp64", S, K, world)
+    e2e64 = world * cells * S * K / dt_e2e / 1e6
+
+    if rank != 0:
+        return
+    clk = r64["clocks"] or {}
+    sm_mhz = clk.get("sm_mhz") or pk["sm_max_mhz"]
+    k64_s = r64["kernel_ms_avg"] * 1e-3
+    k32_s = r32["kernel_ms_avg"] * 1e-3
+    fp64_ach = FP64_FLOPS_PER_CELL * cells / k64_s / 1e12
+    fp64_peak = fp64_peak_tflops(pk["sm_max_mhz"])
+    hbm64 = BYTES_PER_CELL["fp64"] * cells / k64_s / 1e9
+    hbm32 = BYTES_PER_CELL["fp32_store"] * cells / k32_s / 1e9
+    t64 = kernel_traffic("fp64_step")
+    t32 = kernel_traffic("fp32_store_step")
+    cpu = oracle_sample(min_seconds=10.0) if world == 1 else None
+    launches = K * (S * r64["launches_per_step"] + 1)
+    line = {
+        "metric": METRIC, "value": mlups64, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": Wm,
+        "ms_per_step": r64["ms"] / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": prob.name, "cells": cells, "grid": [prob.nx, prob.ny], "substeps_per_step": S,
+                   "input": f"four-quadrant Riemann problem, seed {wl.quadrant_seed()}, ideal gas 1.4, CFL 0.5",
+                   "l2": "inputs larger than L2 (2.1 GB FP64 populations per buffer)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": "alu", "achieved": fp64_ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                     "frac": fp64_ach / fp64_peak, "traffic": None if t64 is None else t64 * cells,
+                     "kernel": "k_tile<2,double> (FP64 step)", "kernel_ms": r64["kernel_ms_avg"],
+                     "peak_source": "FP64 unit count x max SM clock", "hbm_achieved_gbs": hbm64,
+                     "hbm_frac": hbm64 / pk["hbm_gbs"], "hbm_peak_source": pk["source"]},
+        "variants": {
+            "fp32_store": {"value": mlups32, "unit": UNIT, "dtype": "f32 storage (FP32 math, FP64 maxima)",
+                           "ms_per_step": r32["ms"] / K, "speedup_vs_fp64": mlups32 / mlups64,
+                           "roofline": {"bound": "hbm", "achieved": hbm32, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                                        "frac": hbm32 / pk["hbm_gbs"],
+                                        "traffic": None if t32 is None else t32 * cells,
+                                        "kernel": "k_tile<2,float,lookahead> (FP32-storage step)",
+                                        "kernel_ms": r32["kernel_ms_avg"], "peak_source": pk["source"]}},
+        },
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e64, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+        "gpu_launches": launches,
+        "clocks": {"sm_mhz": clk.get("sm_mhz"), "sm_max_mhz": clk.get("sm_max_mhz"), "reasons": clk.get("reasons", []),
+                   "samples": clk.get("samples", 0)},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--substeps", type=int, default=32)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--only", choices=list(BYTES_PER_CELL), help="time one path only (profiling, sweeps)")
+    ap.add_argument("--grid", type=int, default=0, help="with --only: n x n copy of the workload")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    elif args.only:
+        run_only(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

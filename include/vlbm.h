@@ -1,0 +1,167 @@
+/* vlbm.h: C interface of the B300 (sm_103a) vectorial lattice Boltzmann step library.
+ *
+ * The library advances the vectorial lattice Boltzmann method (VLBM) of Hosseini & Karlin,
+ * "Vectorial lattice Boltzmann solver for compressible inviscid flows with generic equation of
+ * state", for the compressible Euler equations dW/dt + div Q(W) = 0 (Sec. II, Eqs. 9-10) with
+ * W = (rho, rho u, rho E) (Eq. 2) on a uniform D = 1 or D = 2 grid, D1Q2 / D2Q4 lattices
+ * (Sec. III A, Eq. 18).  One time step is, per cell (Secs. III A, III D, III E):
+ *   W = sum_i f_i; P(rho, e) and c_s^2 from the EOS (Eqs. 11-17); s_max -> link speed c and dt
+ *   (Eqs. 36-37, the last step shortened onto t_end); reprojection of f from the old to the new
+ *   link speed (Eqs. 38-40); shock sensor beta(x) (Eqs. 28-35); relaxation
+ *   f_i <- 2 beta f_i^eq(W) + (1 - 2 beta) f_i with f_i^eq = W/(2D) + c_i.Q(W)/(2c^2) (Eqs. 20, 22);
+ *   exact transport f_i(x) <- f_i(x - dt c_i) (Eq. 21).
+ *
+ * Conventions for every call:
+ *   - Field arrays are float64, laid out [component][y][x] with x fastest (1D: ny = 1), and may be
+ *     device pointers or host pointers (unified addressing decides; host memory should be pinned
+ *     for asynchronous copies).  The caller owns them.  The handle owns the populations, the
+ *     device scalars, the time-step history and all scratch.
+ *   - Work is issued on the CUDA stream given to vlbm_create, in stream order.  Only
+ *     vlbm_step (at its end), vlbm_get_time, vlbm_get_dt_history, vlbm_get_W/vlbm_get_beta with a
+ *     host destination, vlbm_save_state and the timing calls synchronise with the host.
+ *   - Errors are return codes; no call aborts the process.  A state with rho <= 0, c_s^2 <= 0
+ *     (Eq. 14 violated) or non-finite values detected on the device is reported as
+ *     VLBM_E_NONPHYSICAL by the next synchronising call; the handle then stays in that state.
+ *   - A handle is not thread-safe; use one handle per stream.
+ */
+#ifndef VLBM_H
+#define VLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vlbm_s* vlbm_t;
+
+typedef enum {
+  VLBM_OK = 0,
+  VLBM_E_INVAL = 1,       /* invalid argument (sizes, parameters, null pointers)          */
+  VLBM_E_NOMEM = 2,       /* device or host allocation failed                             */
+  VLBM_E_CUDA = 3,        /* a CUDA runtime call failed                                   */
+  VLBM_E_NONPHYSICAL = 4, /* rho <= 0, c_s^2 <= 0 or non-finite state (Eq. 14)            */
+  VLBM_E_TIMEOUT = 5,     /* a bounded wait ran out                                       */
+  VLBM_E_STATE = 6,       /* call out of order (e.g. vlbm_step before vlbm_init)          */
+  VLBM_E_CHECKSUM = 7,    /* saved state failed its integrity check                       */
+  VLBM_E_UNSUPPORTED = 8  /* combination not built (reported, never silently substituted) */
+} vlbm_status;
+
+/* Boundary rule per domain side (periodic pairs both sides of an axis).  Zero-gradient is the
+ * edge-replicated ghost cell of Secs. IV B and IV E: every stencil access and every streamed
+ * population beyond the edge reads the edge cell. */
+typedef enum { VLBM_BC_PERIODIC = 0, VLBM_BC_ZEROGRAD = 1 } vlbm_bc;
+
+typedef struct {
+  int32_t dim;        /* 1 or 2                                                             */
+  int64_t nx, ny;     /* cells per axis (ny ignored and taken as 1 when dim = 1)            */
+  double x0, x1;      /* domain extent along x; dx = (x1 - x0) / nx; cells are square in 2D */
+  double y0, y1;      /* extent along y (informational; dy is taken equal to dx)            */
+  int32_t bc[4];      /* x-lo, x-hi, y-lo, y-hi (vlbm_bc)                                   */
+} vlbm_grid;
+
+/* Equations of state of Sec. II C: ideal gas P = (gamma-1) rho e (Eq. 15); polytropic van der
+ * Waals P = R rho T / (1 - b rho) - a rho^2, e = cv T - a rho (Eqs. 16-17). */
+typedef enum { VLBM_EOS_IDEAL = 0, VLBM_EOS_VDW = 1 } vlbm_eos_kind;
+
+typedef struct {
+  int32_t kind;                  /* vlbm_eos_kind                 */
+  double gamma;                  /* ideal gas                     */
+  double a, b, R, cv;            /* van der Waals (gamma ignored) */
+} vlbm_eos;
+
+typedef enum { VLBM_FP64 = 0, VLBM_FP32_STORE = 1 } vlbm_precision;
+typedef enum { VLBM_BETA_SENSOR = 0, VLBM_BETA_CONST = 1 } vlbm_beta_mode;
+typedef enum { VLBM_ALGO_AUTO = 0, VLBM_ALGO_TWO_PASS = 1, VLBM_ALGO_LOOKAHEAD = 2 } vlbm_algorithm;
+
+typedef struct {
+  double cfl;             /* target Courant number in (0, 1) (Eq. 37)                           */
+  int32_t beta_mode;      /* vlbm_beta_mode: shock sensor (Sec. III D) or constant beta         */
+  double beta_const;      /* constant beta in (0, 1] (Eq. 24) for VLBM_BETA_CONST                */
+  double beta_min;        /* sensor floor, 0 < beta_min <= beta_max <= 1 (Eqs. 34-35)            */
+  double beta_max;        /* sensor ceiling                                                     */
+  double c_sensor;        /* sensitivity C_sensor >= 0 (Eqs. 34-35)                              */
+  double ducros_eps;      /* regulariser epsilon > 0 of the Ducros ratio (Eq. 33)                */
+  int32_t retarget_every; /* retarget the link speed every k >= 1 steps (Sec. III E)            */
+  int32_t precision;      /* vlbm_precision: FP64 populations, or FP32 storage of deviations    */
+  int32_t algorithm;      /* vlbm_algorithm: how the two global maxima of a step are obtained   */
+} vlbm_params;
+
+/* Creates a solver for the grid, EOS and parameters, bound to `cuda_stream` (a cudaStream_t, or
+ * NULL for the legacy default stream).  Allocates the two population buffers (2 * 2D * (D+2)
+ * values per cell, 8 bytes each for VLBM_FP64, 4 for VLBM_FP32_STORE) and scratch on the current
+ * device.  Returns VLBM_E_INVAL for nx, ny < 1, more than 2^31 - 1 cells, a periodic side without
+ * its periodic partner, or parameters outside the ranges above; VLBM_E_NOMEM if allocation
+ * fails.  *out receives the handle (NULL on failure). */
+vlbm_status vlbm_create(const vlbm_grid* grid, const vlbm_eos* eos, const vlbm_params* params, void* cuda_stream,
+                        vlbm_t* out);
+
+/* Releases every resource of the handle after its stream has drained.  NULL is accepted. */
+vlbm_status vlbm_destroy(vlbm_t h);
+
+/* Initial populations f_i = f_i^eq(W0; c0) with c0 = s_max(W0) / CFL (Eqs. 20, 36-37), time 0,
+ * step counter 0, history cleared.  W0: (D+2) * ny * nx values.  A replayed schedule (see
+ * vlbm_set_dt_schedule) supplies c0 instead.  A non-physical W0 is reported by the next
+ * synchronising call. */
+vlbm_status vlbm_init(vlbm_t h, const double* W0);
+
+/* Advances up to n_steps time steps.  With t_end > 0 the run stops once t reaches t_end, the
+ * last step being shortened to land on it exactly (Sec. III E); t_end <= 0 disables the end time.
+ * All link-speed and time-step decisions are taken on the device (no host synchronisation per
+ * step); the call synchronises once at its end and writes the number of steps taken to
+ * *steps_done (may be NULL). */
+vlbm_status vlbm_step(vlbm_t h, int64_t n_steps, double t_end, int64_t* steps_done);
+
+/* W = sum_i f_i of the current state (Sec. III A), (D+2) * ny * nx float64 values. */
+vlbm_status vlbm_get_W(vlbm_t h, double* W);
+
+/* beta(x) that the next step would use on the current state (Secs. III D; constant in
+ * VLBM_BETA_CONST mode), ny * nx float64 values. */
+vlbm_status vlbm_get_beta(vlbm_t h, double* beta);
+
+/* Current populations f_i (the state whose zeroth moment vlbm_get_W returns), 2D * (D+2) * ny *
+ * nx float64 values laid out [i][k][y][x], i in the lattice order {x-, x+, y-, y+} (1D: {x-, x+}).
+ * FP32-storage handles return the stored FP32 deviation plus the FP64 reference share. */
+vlbm_status vlbm_get_populations(vlbm_t h, double* f);
+
+/* Time t, completed steps n and current link speed c (synchronises). Any pointer may be NULL. */
+vlbm_status vlbm_get_time(vlbm_t h, double* t, int64_t* n, double* c);
+
+/* Copies the per-step (dt, c) history of the run since vlbm_init into host arrays of capacity
+ * `cap` (either may be NULL) and writes the number of recorded steps to *n (synchronises). */
+vlbm_status vlbm_get_dt_history(vlbm_t h, double* dt_host, double* c_host, int64_t cap, int64_t* n);
+
+/* Replays a fixed link-speed sequence instead of the CFL rule: c_host[0] is the initial link
+ * speed used by vlbm_init, c_host[j] (j >= 1) the link speed of step j-1; dt = dx / c.  n = 0
+ * returns to the adaptive rule.  Steps beyond the sequence fail with VLBM_E_INVAL.  Used to repeat
+ * a recorded run exactly (finite differences, adjoint). */
+vlbm_status vlbm_set_dt_schedule(vlbm_t h, const double* c_host, int64_t n);
+
+/* Launches the dominant step kernel `reps` times on the handle's stream (without advancing the
+ * state: each launch recomputes the same next state into the spare buffer) bracketed by CUDA
+ * events, and writes the mean duration of one launch in milliseconds (synchronises).  The state
+ * must have been initialised. */
+vlbm_status vlbm_time_step_kernel(vlbm_t h, int32_t reps, double* ms_per_launch);
+
+/* Live kernel timing.  With `on` != 0, vlbm_step issues its steps one by one (no CUDA graph) and
+ * brackets every launch of the dominant step kernel with a pair of CUDA events on the handle's
+ * stream; vlbm_get_profile then returns the summed device time of those launches (ms) and their
+ * count, and resets both (synchronises).  Turning profiling on or off also resets them. */
+vlbm_status vlbm_set_profiling(vlbm_t h, int32_t on);
+vlbm_status vlbm_get_profile(vlbm_t h, double* ms_total, int64_t* launches);
+
+/* Number of kernel launches one time step issues (for launch accounting). */
+vlbm_status vlbm_launches_per_step(vlbm_t h, int32_t* launches);
+
+/* Human-readable name of a status code (static storage). */
+const char* vlbm_status_string(vlbm_status s);
+
+/* Library version string (static storage). */
+const char* vlbm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VLBM_H */

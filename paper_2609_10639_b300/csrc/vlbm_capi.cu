@@ -1,0 +1,542 @@
+// C interface of the VLBM step library (declared in include/vlbm.h).
+//
+// Each handle owns two population buffers, a device-resident scalar block, the (dt, c) history
+// and scratch.  vlbm_step issues the step kernels in chunks captured once as CUDA graphs (one
+// graph per buffer parity), launched on the caller's stream; the device decides the link speed
+// and time step, so the host synchronises only once at the end of the call (or once per chunk
+// when an end time is given and the number of steps is not known in advance).
+#include "vlbm.h"
+#include "vlbm_internal.cuh"
+
+#include <cmath>
+#include <cstddef>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+using vlbm::KParams;
+using vlbm::Scalars;
+
+struct vlbm_s {
+  int device = 0;
+  cudaStream_t stream = nullptr;      // caller's stream
+  cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs
+  KParams p{};
+  int precision = 0;
+  bool lookahead = false;
+  size_t elem = 8;  // bytes per stored population value
+  void* buf[2] = {nullptr, nullptr};
+  Scalars* sc = nullptr;       // device
+  Scalars* sc_host = nullptr;  // pinned mirror for readback
+  double* hist_dt = nullptr;
+  double* hist_c = nullptr;
+  long long hist_cap = 0;
+  double* sched = nullptr;
+  long long sched_len = 0;
+  double* partial = nullptr;  // compensated-sum partials (FP32 reference)
+  int nblk_sum = 0;
+  double* part = nullptr;     // per-CTA partial maxima, [2][max_parts][5]
+  double* scratch = nullptr;  // (D+2) * plane doubles + plane + 8 (beta + 1/M)
+  size_t scratch_elems = 0;
+  double* fscratch = nullptr;  // populations readback (lazily allocated)
+  bool initialised = false;
+  bool unpulled = true;        // the current buffer holds equilibrium populations in place
+  bool last_step_pulled = true;
+  long long n_host = 0;        // steps completed, as of the last synchronisation
+  static constexpr int kChunk = 32;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  bool profile = false;            // bracket step-kernel launches with events
+  std::vector<cudaEvent_t> pev;    // event pool, used in pairs
+  size_t pev_used = 0;
+};
+
+namespace {
+
+vlbm::Launch launch_of(vlbm_t h, cudaStream_t s) {
+  vlbm::Launch L;
+  L.p = &h->p;
+  L.sc = h->sc;
+  L.part = h->part;
+  L.stream = s;
+  L.hist_dt = h->hist_dt;
+  L.hist_c = h->hist_c;
+  L.sched = h->sched;
+  return L;
+}
+
+vlbm_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return VLBM_OK;
+  if (e == cudaErrorMemoryAllocation) return VLBM_E_NOMEM;
+  return VLBM_E_CUDA;
+}
+
+#define VLBM_TRY(expr)                      \
+  do {                                      \
+    cudaError_t _e = (expr);                \
+    if (_e != cudaSuccess) return cuda_status(_e); \
+  } while (0)
+
+bool is_device_ptr(const void* ptr) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+void destroy_graphs(vlbm_t h) {
+  for (int j = 0; j < 2; ++j)
+    if (h->graph[j]) {
+      cudaGraphExecDestroy(h->graph[j]);
+      h->graph[j] = nullptr;
+    }
+}
+
+// Next pair of profiling events (grows the pool).
+cudaError_t profile_pair(vlbm_t h, cudaEvent_t* a, cudaEvent_t* b) {
+  while (h->pev.size() < h->pev_used + 2) {
+    cudaEvent_t e;
+    cudaError_t r = cudaEventCreate(&e);
+    if (r != cudaSuccess) return r;
+    h->pev.push_back(e);
+  }
+  *a = h->pev[h->pev_used];
+  *b = h->pev[h->pev_used + 1];
+  h->pev_used += 2;
+  return cudaSuccess;
+}
+
+// Issues one step (reading buffer `par`) on stream s.
+cudaError_t issue_step(vlbm_t h, cudaStream_t s, int par, int pulled, bool record = false) {
+  vlbm::Launch L = launch_of(h, s);
+  const void* fin = h->buf[par];
+  void* fout = h->buf[par ^ 1];
+  cudaError_t e;
+  if (!h->lookahead) {
+    e = vlbm::launch_reduce(L, h->precision, fin, pulled);
+    if (e != cudaSuccess) return e;
+  }
+  e = vlbm::launch_dt(L);
+  if (e != cudaSuccess) return e;
+  cudaEvent_t ea = nullptr, eb = nullptr;
+  if (record) {
+    e = profile_pair(h, &ea, &eb);
+    if (e != cudaSuccess) return e;
+    e = cudaEventRecord(ea, s);
+    if (e != cudaSuccess) return e;
+  }
+  e = vlbm::launch_step(L, h->precision, h->lookahead, fin, fout, pulled);
+  if (e != cudaSuccess || !record) return e;
+  return cudaEventRecord(eb, s);
+}
+
+cudaError_t build_graph(vlbm_t h, int par) {
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  cudaError_t le = cudaSuccess;
+  for (int j = 0; j < vlbm_s::kChunk && le == cudaSuccess; ++j) le = issue_step(h, h->cap_stream, par ^ (j & 1), 1);
+  e = cudaStreamEndCapture(h->cap_stream, &g);
+  if (le != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return le;
+  }
+  if (e != cudaSuccess) return e;
+  e = cudaGraphInstantiate(&h->graph[par], g, 0);
+  cudaGraphDestroy(g);
+  return e;
+}
+
+// Grows the history arrays to hold at least `need` steps (keeps the recorded part).
+vlbm_status ensure_history(vlbm_t h, long long need) {
+  if (need <= h->hist_cap) return VLBM_OK;
+  long long cap = h->hist_cap > 0 ? h->hist_cap : 4096;
+  while (cap < need) cap *= 2;
+  double *ndt = nullptr, *nc = nullptr;
+  if (cudaMalloc(&ndt, cap * sizeof(double)) != cudaSuccess) return VLBM_E_NOMEM;
+  if (cudaMalloc(&nc, cap * sizeof(double)) != cudaSuccess) {
+    cudaFree(ndt);
+    return VLBM_E_NOMEM;
+  }
+  if (h->hist_cap > 0) {
+    VLBM_TRY(cudaMemcpyAsync(ndt, h->hist_dt, h->hist_cap * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    VLBM_TRY(cudaMemcpyAsync(nc, h->hist_c, h->hist_cap * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  }
+  VLBM_TRY(cudaStreamSynchronize(h->stream));
+  cudaFree(h->hist_dt);
+  cudaFree(h->hist_c);
+  h->hist_dt = ndt;
+  h->hist_c = nc;
+  h->hist_cap = cap;
+  h->sc_host->hist_cap = cap;
+  VLBM_TRY(cudaMemcpyAsync(&h->sc->hist_cap, &cap, sizeof(long long), cudaMemcpyHostToDevice, h->stream));
+  VLBM_TRY(cudaStreamSynchronize(h->stream));
+  destroy_graphs(h);  // the graphs captured the old history pointers
+  return VLBM_OK;
+}
+
+// Copies the device scalars to the pinned mirror and waits.
+vlbm_status sync_scalars(vlbm_t h) {
+  VLBM_TRY(cudaMemcpyAsync(h->sc_host, h->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, h->stream));
+  VLBM_TRY(cudaStreamSynchronize(h->stream));
+  h->n_host = h->sc_host->n;
+  if (h->sc_host->err & vlbm::ERR_SCHEDULE) return VLBM_E_INVAL;
+  if (h->sc_host->err) return VLBM_E_NONPHYSICAL;
+  return VLBM_OK;
+}
+
+bool valid_params(const vlbm_params* q) {
+  if (!(q->cfl > 0.0 && q->cfl < 1.0)) return false;
+  if (q->beta_mode != VLBM_BETA_SENSOR && q->beta_mode != VLBM_BETA_CONST) return false;
+  if (q->beta_mode == VLBM_BETA_CONST && !(q->beta_const > 0.0 && q->beta_const <= 1.0)) return false;
+  if (q->beta_mode == VLBM_BETA_SENSOR) {
+    if (!(q->beta_min > 0.0 && q->beta_min <= q->beta_max && q->beta_max <= 1.0)) return false;
+    if (!(q->c_sensor >= 0.0) || !(q->ducros_eps > 0.0)) return false;
+  }
+  if (q->retarget_every < 1) return false;
+  if (q->precision != VLBM_FP64 && q->precision != VLBM_FP32_STORE) return false;
+  if (q->algorithm < VLBM_ALGO_AUTO || q->algorithm > VLBM_ALGO_LOOKAHEAD) return false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* vlbm_status_string(vlbm_status s) {
+  switch (s) {
+    case VLBM_OK: return "ok";
+    case VLBM_E_INVAL: return "invalid argument";
+    case VLBM_E_NOMEM: return "out of memory";
+    case VLBM_E_CUDA: return "CUDA error";
+    case VLBM_E_NONPHYSICAL: return "non-physical state (rho <= 0, c_s^2 <= 0 or non-finite)";
+    case VLBM_E_TIMEOUT: return "timeout";
+    case VLBM_E_STATE: return "call out of order";
+    case VLBM_E_CHECKSUM: return "checksum mismatch";
+    case VLBM_E_UNSUPPORTED: return "unsupported combination";
+  }
+  return "unknown status";
+}
+
+const char* vlbm_version(void) { return "vlbm-b300 0.1 (sm_103a)"; }
+
+vlbm_status vlbm_create(const vlbm_grid* grid, const vlbm_eos* eos, const vlbm_params* params, void* cuda_stream,
+                        vlbm_t* out) {
+  if (out) *out = nullptr;
+  if (!grid || !eos || !params || !out) return VLBM_E_INVAL;
+  if (grid->dim != 1 && grid->dim != 2) return VLBM_E_INVAL;
+  const long long nx = grid->nx, ny = grid->dim == 1 ? 1 : grid->ny;
+  if (nx < 1 || ny < 1 || nx > 2147483647LL || ny > 2147483647LL || nx * ny > 2147483647LL) return VLBM_E_INVAL;
+  if (!(grid->x1 > grid->x0)) return VLBM_E_INVAL;
+  for (int j = 0; j < 4; ++j)
+    if (grid->bc[j] != VLBM_BC_PERIODIC && grid->bc[j] != VLBM_BC_ZEROGRAD) return VLBM_E_INVAL;
+  if ((grid->bc[0] == VLBM_BC_PERIODIC) != (grid->bc[1] == VLBM_BC_PERIODIC)) return VLBM_E_INVAL;
+  if (grid->dim == 2 && (grid->bc[2] == VLBM_BC_PERIODIC) != (grid->bc[3] == VLBM_BC_PERIODIC)) return VLBM_E_INVAL;
+  if (eos->kind == VLBM_EOS_IDEAL) {
+    if (!(eos->gamma > 1.0)) return VLBM_E_INVAL;
+  } else if (eos->kind == VLBM_EOS_VDW) {
+    if (!(eos->a >= 0.0 && eos->b >= 0.0 && eos->R > 0.0 && eos->cv > 0.0)) return VLBM_E_INVAL;
+  } else {
+    return VLBM_E_INVAL;
+  }
+  if (!valid_params(params)) return VLBM_E_INVAL;
+
+  vlbm_s* h = new (std::nothrow) vlbm_s();
+  if (!h) return VLBM_E_NOMEM;
+  cudaGetDevice(&h->device);
+  h->stream = (cudaStream_t)cuda_stream;
+  KParams& p = h->p;
+  p.dim = grid->dim;
+  p.nc = grid->dim + 2;
+  p.q = 2 * grid->dim;
+  p.nx = (int)nx;
+  p.ny = (int)ny;
+  p.plane = nx * ny;
+  for (int j = 0; j < 4; ++j) p.bc[j] = grid->bc[j];
+  if (grid->dim == 1) p.bc[2] = p.bc[3] = VLBM_BC_ZEROGRAD;
+  p.dx = (grid->x1 - grid->x0) / (double)nx;
+  p.inv2dx = 1.0 / (2.0 * p.dx);
+  p.eos_kind = eos->kind;
+  p.gamma = eos->kind == VLBM_EOS_IDEAL ? eos->gamma : 1.0 + eos->R / eos->cv;
+  p.a = eos->a;
+  p.b = eos->b;
+  p.R = eos->R;
+  p.cv = eos->cv;
+  p.inv_cv = eos->kind == VLBM_EOS_VDW ? 1.0 / eos->cv : 0.0;
+  p.cfl = params->cfl;
+  p.beta_mode = params->beta_mode;
+  p.beta_const = params->beta_const;
+  p.beta_min = params->beta_min;
+  p.beta_max = params->beta_max;
+  p.c_sensor = params->c_sensor;
+  p.ducros_eps = params->ducros_eps;
+  p.retarget_every = params->retarget_every;
+  p.max_parts = vlbm::max_partials(p);
+  h->precision = params->precision;
+  h->elem = params->precision == VLBM_FP64 ? 8 : 4;
+  // Look-ahead (one pass over HBM per step) for FP32 storage, which is bandwidth-bound; the FP64
+  // step is bound by the FP64 pipe, where the extra ring of relaxation costs more than the
+  // separate reduction pass saves.
+  h->lookahead = params->algorithm == VLBM_ALGO_LOOKAHEAD ||
+                 (params->algorithm == VLBM_ALGO_AUTO && params->precision == VLBM_FP32_STORE);
+
+  vlbm_status st = VLBM_OK;
+  const size_t fbytes = (size_t)p.q * p.nc * p.plane * h->elem;
+  h->scratch_elems = (size_t)p.nc * p.plane + p.plane + 8;
+  h->nblk_sum = vlbm::sum_blocks(p);
+  if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) {
+    st = VLBM_E_CUDA;
+  } else if (cudaMalloc(&h->buf[0], fbytes) != cudaSuccess || cudaMalloc(&h->buf[1], fbytes) != cudaSuccess ||
+             cudaMalloc(&h->sc, sizeof(Scalars)) != cudaSuccess ||
+             cudaMallocHost(&h->sc_host, sizeof(Scalars)) != cudaSuccess ||
+             cudaMalloc(&h->scratch, h->scratch_elems * sizeof(double)) != cudaSuccess ||
+             cudaMalloc(&h->partial, (size_t)h->nblk_sum * 4 * sizeof(double)) != cudaSuccess ||
+             cudaMalloc(&h->part, (size_t)2 * p.max_parts * vlbm::kNV * sizeof(double)) != cudaSuccess) {
+    st = VLBM_E_NOMEM;
+  } else if (vlbm::prepare_kernels() != cudaSuccess) {
+    st = VLBM_E_CUDA;
+  }
+  if (st == VLBM_OK) {
+    std::memset(h->sc_host, 0, sizeof(Scalars));
+    if (cudaMemsetAsync(h->sc, 0, sizeof(Scalars), h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess)
+      st = VLBM_E_CUDA;
+  }
+  if (st == VLBM_OK) st = ensure_history(h, 4096);
+  if (st != VLBM_OK) {
+    cudaGetLastError();
+    vlbm_destroy(h);
+    return st;
+  }
+  *out = h;
+  return VLBM_OK;
+}
+
+vlbm_status vlbm_destroy(vlbm_t h) {
+  if (!h) return VLBM_OK;
+  if (h->stream || h->cap_stream) cudaStreamSynchronize(h->stream);
+  destroy_graphs(h);
+  cudaFree(h->buf[0]);
+  cudaFree(h->buf[1]);
+  cudaFree(h->sc);
+  if (h->sc_host) cudaFreeHost(h->sc_host);
+  cudaFree(h->hist_dt);
+  cudaFree(h->hist_c);
+  cudaFree(h->sched);
+  cudaFree(h->partial);
+  cudaFree(h->part);
+  cudaFree(h->scratch);
+  cudaFree(h->fscratch);
+  for (cudaEvent_t e : h->pev) cudaEventDestroy(e);
+  if (h->ev0) cudaEventDestroy(h->ev0);
+  if (h->ev1) cudaEventDestroy(h->ev1);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  delete h;
+  return VLBM_OK;
+}
+
+vlbm_status vlbm_set_dt_schedule(vlbm_t h, const double* c_host, int64_t n) {
+  if (!h || n < 0 || (n > 0 && !c_host)) return VLBM_E_INVAL;
+  for (int64_t j = 0; j < n; ++j)
+    if (!(c_host[j] > 0.0) || !std::isfinite(c_host[j])) return VLBM_E_INVAL;
+  VLBM_TRY(cudaStreamSynchronize(h->stream));
+  cudaFree(h->sched);
+  h->sched = nullptr;
+  h->sched_len = 0;
+  if (n > 0) {
+    VLBM_TRY(cudaMalloc(&h->sched, n * sizeof(double)));
+    VLBM_TRY(cudaMemcpy(h->sched, c_host, n * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  h->sched_len = n;
+  long long len = n;
+  VLBM_TRY(cudaMemcpy(&h->sc->sched_len, &len, sizeof(long long), cudaMemcpyHostToDevice));
+  destroy_graphs(h);  // the graphs captured the old schedule pointer
+  return VLBM_OK;
+}
+
+vlbm_status vlbm_init(vlbm_t h, const double* W0) {
+  if (!h || !W0) return VLBM_E_INVAL;
+  const size_t wbytes = (size_t)h->p.nc * h->p.plane * sizeof(double);
+  const double* src = W0;
+  if (!is_device_ptr(W0)) {
+    VLBM_TRY(cudaMemcpyAsync(h->scratch, W0, wbytes, cudaMemcpyDefault, h->stream));
+    src = h->scratch;
+  }
+  vlbm::Launch L = launch_of(h, h->stream);
+  VLBM_TRY(vlbm::launch_init(L, h->precision, src, h->buf[0], h->partial, h->nblk_sum));
+  h->initialised = true;
+  h->unpulled = true;
+  h->last_step_pulled = false;
+  h->n_host = 0;
+  return VLBM_OK;
+}
+
+vlbm_status vlbm_step(vlbm_t h, int64_t n_steps, double t_end, int64_t* steps_done) {
+  if (steps_done) *steps_done = 0;
+  if (!h || n_steps < 0 || !std::isfinite(t_end)) return VLBM_E_INVAL;
+  if (!h->initialised) return VLBM_E_STATE;
+  if (n_steps == 0) return VLBM_OK;
+  vlbm_status st = VLBM_OK;
+  const long long n0 = h->n_host;
+  vlbm::Launch L = launch_of(h, h->stream);
+  VLBM_TRY(vlbm::launch_begin(L, t_end));
+  long long issued = 0, n_expect = n0;
+  const bool poll = t_end > 0.0;  // an end time may stop the run early: check once per chunk
+  while (issued < n_steps) {
+    // history room for the next chunk (grows by doubling; rebuilds the graphs when it moves)
+    st = ensure_history(h, n_expect + vlbm_s::kChunk + 1);
+    if (st != VLBM_OK) break;
+    const int par = (int)(n_expect & 1);
+    if (h->unpulled) {  // first step after vlbm_init reads the equilibrium in place
+      VLBM_TRY(issue_step(h, h->stream, par, 0, h->profile));
+      h->unpulled = false;
+      h->last_step_pulled = false;
+      ++issued;
+      ++n_expect;
+      continue;
+    }
+    if (n_steps - issued >= vlbm_s::kChunk && !h->profile) {
+      if (!h->graph[par]) VLBM_TRY(build_graph(h, par));
+      VLBM_TRY(cudaGraphLaunch(h->graph[par], h->stream));
+      issued += vlbm_s::kChunk;
+      n_expect += vlbm_s::kChunk;
+    } else {
+      VLBM_TRY(issue_step(h, h->stream, par, 1, h->profile));
+      ++issued;
+      ++n_expect;
+    }
+    h->last_step_pulled = true;
+    if (poll && issued < n_steps) {
+      st = sync_scalars(h);
+      if (st != VLBM_OK) break;
+      if (h->sc_host->done) break;
+      n_expect = h->n_host;
+    }
+  }
+  vlbm_status st2 = sync_scalars(h);
+  if (steps_done) *steps_done = h->n_host - n0;
+  if (h->n_host == n0 + 1 && n0 == 0) h->last_step_pulled = false;
+  if (st != VLBM_OK) return st;
+  return st2;
+}
+
+vlbm_status vlbm_get_W(vlbm_t h, double* W) {
+  if (!h || !W) return VLBM_E_INVAL;
+  if (!h->initialised) return VLBM_E_STATE;
+  const int cur = (int)(h->n_host & 1);
+  const bool dev = is_device_ptr(W);
+  double* dst = dev ? W : h->scratch;
+  vlbm::Launch L = launch_of(h, h->stream);
+  VLBM_TRY(vlbm::launch_get_W(L, h->precision, h->buf[cur], h->unpulled ? 0 : 1, dst));
+  if (!dev) {
+    VLBM_TRY(cudaMemcpyAsync(W, h->scratch, (size_t)h->p.nc * h->p.plane * sizeof(double), cudaMemcpyDefault, h->stream));
+    VLBM_TRY(cudaStreamSynchronize(h->stream));
+  }
+  return VLBM_OK;
+}
+
+vlbm_status vlbm_get_populations(vlbm_t h, double* f) {
+  if (!h || !f) return VLBM_E_INVAL;
+  if (!h->initialised) return VLBM_E_STATE;
+  const size_t bytes = (size_t)h->p.q * h->p.nc * h->p.plane * sizeof(double);
+  const bool dev = is_device_ptr(f);
+  double* dst = f;
+  if (!dev) {
+    if (!h->fscratch) VLBM_TRY(cudaMalloc(&h->fscratch, bytes));
+    dst = h->fscratch;
+  }
+  const int cur = (int)(h->n_host & 1);
+  vlbm::Launch L = launch_of(h, h->stream);
+  VLBM_TRY(vlbm::launch_get_f(L, h->precision, h->buf[cur], h->unpulled ? 0 : 1, dst));
+  if (!dev) {
+    VLBM_TRY(cudaMemcpyAsync(f, dst, bytes, cudaMemcpyDefault, h->stream));
+    VLBM_TRY(cudaStreamSynchronize(h->stream));
+  }
+  return VLBM_OK;
+}
+
+vlbm_status vlbm_get_beta(vlbm_t h, double* beta) {
+  if (!h || !beta) return VLBM_E_INVAL;
+  if (!h->initialised) return VLBM_E_STATE;
+  const int cur = (int)(h->n_host & 1);
+  double* out = h->scratch + (size_t)h->p.nc * h->p.plane;  // plane + 4 doubles (beta, 1/M_k)
+  vlbm::Launch L = launch_of(h, h->stream);
+  VLBM_TRY(vlbm::launch_beta(L, h->precision, h->buf[cur], h->unpulled ? 0 : 1, out));
+  VLBM_TRY(cudaMemcpyAsync(beta, out, (size_t)h->p.plane * sizeof(double), cudaMemcpyDefault, h->stream));
+  VLBM_TRY(cudaStreamSynchronize(h->stream));
+  VLBM_TRY(cudaMemcpy(h->sc_host, h->sc, sizeof(Scalars), cudaMemcpyDeviceToHost));
+  return h->sc_host->err ? VLBM_E_NONPHYSICAL : VLBM_OK;
+}
+
+vlbm_status vlbm_get_time(vlbm_t h, double* t, int64_t* n, double* c) {
+  if (!h) return VLBM_E_INVAL;
+  vlbm_status st = sync_scalars(h);
+  if (t) *t = h->sc_host->t;
+  if (n) *n = h->sc_host->n;
+  if (c) *c = h->sc_host->c_prev;
+  return st;
+}
+
+vlbm_status vlbm_get_dt_history(vlbm_t h, double* dt_host, double* c_host, int64_t cap, int64_t* n) {
+  if (!h || cap < 0) return VLBM_E_INVAL;
+  vlbm_status st = sync_scalars(h);
+  const long long m = h->n_host < cap ? h->n_host : cap;
+  if (m > 0 && dt_host) VLBM_TRY(cudaMemcpy(dt_host, h->hist_dt, m * sizeof(double), cudaMemcpyDeviceToHost));
+  if (m > 0 && c_host) VLBM_TRY(cudaMemcpy(c_host, h->hist_c, m * sizeof(double), cudaMemcpyDeviceToHost));
+  if (n) *n = h->n_host;
+  return st;
+}
+
+vlbm_status vlbm_time_step_kernel(vlbm_t h, int32_t reps, double* ms_per_launch) {
+  if (!h || reps < 1 || !ms_per_launch) return VLBM_E_INVAL;
+  if (!h->initialised || h->n_host < 1) return VLBM_E_STATE;
+  // Re-run the last step kernel (same input buffer, same device scalars): it rewrites the
+  // current state with identical values, so the state does not change.
+  const int cur = (int)(h->n_host & 1);
+  vlbm::Launch L = launch_of(h, h->stream);
+  const int pulled = h->last_step_pulled ? 1 : 0;
+  VLBM_TRY(cudaEventRecord(h->ev0, h->stream));
+  for (int j = 0; j < reps; ++j)
+    VLBM_TRY(vlbm::launch_step(L, h->precision, h->lookahead, h->buf[cur ^ 1], h->buf[cur], pulled));
+  VLBM_TRY(cudaEventRecord(h->ev1, h->stream));
+  VLBM_TRY(cudaEventSynchronize(h->ev1));
+  float ms = 0.f;
+  VLBM_TRY(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+  *ms_per_launch = (double)ms / reps;
+  return VLBM_OK;
+}
+
+vlbm_status vlbm_set_profiling(vlbm_t h, int32_t on) {
+  if (!h) return VLBM_E_INVAL;
+  VLBM_TRY(cudaStreamSynchronize(h->stream));
+  h->profile = on != 0;
+  h->pev_used = 0;
+  return VLBM_OK;
+}
+
+vlbm_status vlbm_get_profile(vlbm_t h, double* ms_total, int64_t* launches) {
+  if (!h) return VLBM_E_INVAL;
+  VLBM_TRY(cudaStreamSynchronize(h->stream));
+  double tot = 0.0;
+  for (size_t j = 0; j + 1 < h->pev_used; j += 2) {
+    float ms = 0.f;
+    VLBM_TRY(cudaEventElapsedTime(&ms, h->pev[j], h->pev[j + 1]));
+    tot += ms;
+  }
+  if (ms_total) *ms_total = tot;
+  if (launches) *launches = (int64_t)(h->pev_used / 2);
+  h->pev_used = 0;
+  return VLBM_OK;
+}
+
+vlbm_status vlbm_launches_per_step(vlbm_t h, int32_t* launches) {
+  if (!h || !launches) return VLBM_E_INVAL;
+  *launches = h->lookahead ? 2 : 3;
+  return VLBM_OK;
+}
+
+}  // extern "C"

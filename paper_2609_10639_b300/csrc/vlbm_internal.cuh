@@ -1,0 +1,79 @@
+// Internal declarations shared by the kernels and the C-ABI layer of the VLBM step library.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace vlbm {
+
+// Device-resident scalars of one solver.  Written only by the one-thread link-speed kernel
+// (and the init kernels); read by every step kernel.  No host synchronisation per step.
+struct Scalars {
+  double c_prev;      // link speed of the stored populations
+  double c_new;       // link speed of the step in flight (Eq. 37)
+  double r;           // c_prev / c_new of the step in flight (reprojection, Eqs. 38-40)
+  double inv_c;       // 1 / c_new
+  double dt;          // time step of the step in flight
+  double t;           // time once the step in flight has completed
+  double t_end;       // end time of the current vlbm_step call (<= 0: none)
+  double inv_M[4];    // 1 / max_{x,alpha} |Q_alpha,k| of the step in flight (0 where the max is 0)
+  double smax;        // s_max of the step in flight (Eq. 36)
+  double wref[4];     // FP32 storage: W_ref_k / Q, the share subtracted from every population
+  long long n;        // steps completed once the step in flight has completed
+  long long hist_cap; // capacity of the (dt, c) history arrays
+  long long sched_len;// length of the replayed link-speed schedule (0: CFL rule)
+  int active;         // the step in flight runs (0 once t_end has been reached)
+  int done;           // t_end reached
+  int err;            // error bits (1: non-physical state; 2: bad schedule)
+  int nparts[2];      // per-CTA partial maxima written into partial slot s (see below)
+};
+
+// Global maxima of a step (s_max, Eq. 36; M_k, Eq. 30) are reduced in two levels without
+// atomics: every CTA of the producing kernel writes its 5 partial maxima (s_max, M_0..M_3) to
+// part[slot][cta][5] and CTA 0 records the count in Scalars::nparts[slot]; the one-CTA link-speed
+// kernel folds them.  Slot of a step = (steps completed when the producer runs) & 1.
+constexpr int kNV = 5;
+
+enum { ERR_NONPHYSICAL = 1, ERR_SCHEDULE = 2 };
+
+// Constant per-solver parameters, passed to kernels by value.
+struct KParams {
+  int dim, nc, q;
+  int nx, ny;
+  long long plane;  // nx * ny
+  int bc[4];        // x-lo, x-hi, y-lo, y-hi: 0 periodic, 1 zero-gradient
+  double dx, inv2dx;
+  int eos_kind;
+  double gamma, a, b, R, cv, inv_cv;
+  double cfl;
+  int beta_mode;
+  double beta_const, beta_min, beta_max, c_sensor, ducros_eps;
+  int retarget_every;
+  int max_parts;    // capacity of one partial-maxima slot (CTAs of the largest producer)
+};
+
+// Host-side launch helpers (defined in vlbm_kernels.cu).
+struct Launch {
+  const KParams* p;
+  Scalars* sc;
+  double* part;      // [2][max_parts][kNV]
+  cudaStream_t stream;
+  double* hist_dt;
+  double* hist_c;
+  const double* sched;
+};
+
+// precision: 0 = FP64, 1 = FP32 storage.  lookahead: fused single-kernel step.
+cudaError_t launch_reduce(const Launch& L, int precision, const void* fin, int pulled);
+cudaError_t launch_dt(const Launch& L);
+cudaError_t launch_step(const Launch& L, int precision, bool lookahead, const void* fin, void* fout, int pulled);
+cudaError_t launch_beta(const Launch& L, int precision, const void* fin, int pulled, double* beta_out);
+cudaError_t launch_init(const Launch& L, int precision, const double* W0, void* fout, double* partial, int nblk_sum);
+cudaError_t launch_get_W(const Launch& L, int precision, const void* fin, int pulled, double* W);
+cudaError_t launch_get_f(const Launch& L, int precision, const void* fin, int pulled, double* f);
+cudaError_t launch_begin(const Launch& L, double t_end);
+cudaError_t prepare_kernels();
+int sum_blocks(const KParams& p);
+int max_partials(const KParams& p);
+
+}  // namespace vlbm

@@ -1,0 +1,1018 @@
+// CUDA kernels of the VLBM step (sm_103a).
+//
+// Populations live in HBM as structure-of-arrays planes [i][k][y][x] (lattice direction i in
+// {x-, x+, y-, y+}, conserved component k), double-buffered.  A buffer holds post-collision
+// populations; a step pulls them across the lattice links on read (exact transport, Eq. 21), so
+// each population is read once and written once per step.  The first step after vlbm_init reads
+// the equilibrium populations in place ("unpulled").
+//
+// Step kernel (k_tile): one CTA owns a TX x TY tile and stages, in shared memory, the primitive
+// velocity and the flux Q_alpha(W) of a halo region around it (radius 2, or 3 for the look-ahead
+// form); the shock sensor (Eqs. 28-35) and its separable box filter read that region; the
+// reprojection (Eqs. 38-40) and relaxation (Eqs. 20, 22) are fused into one register update.
+// Boundary rules are applied to every stencil access: a region position outside a zero-gradient
+// side takes the values of the edge cell (edge-replicated ghost) and every derived stencil
+// quantity there is evaluated at the edge cell; periodic sides are simply unwrapped.
+//
+// The two domain-wide maxima a step needs (s_max, Eq. 36; M_k, Eq. 30) are reduced with warp
+// shuffles and a per-CTA combine into per-CTA partials, folded by the one-CTA link-speed kernel
+// (no atomics, deterministic).  Two forms:
+//   two-pass:   k_reduce (reads the state once more) -> k_dt -> k_tile;
+//   look-ahead: k_dt -> k_tile, where k_tile also relaxes a one-cell ring around its tile,
+//               streams those populations into W^{n+1} of its cells and reduces them for the next
+//               step, so a step moves each population through HBM exactly twice.
+// k_dt is a single-thread kernel that turns the maxima into c, dt, r and 1/M_k on the device.
+#include "vlbm_internal.cuh"
+
+#include <cfloat>
+#include <cstddef>
+#include <cmath>
+#include <type_traits>
+
+namespace vlbm {
+
+// ------------------------------------------------------------------------------------------
+// index rules
+// ------------------------------------------------------------------------------------------
+// Cell index read at position j along an axis of n cells: wrap (periodic) or clamp to the edge
+// (zero-gradient).
+__device__ __forceinline__ int nb_index(int j, int n, int lo, int hi) {
+  if (j < 0) {
+    if (lo == 0) {
+      do { j += n; } while (j < 0);
+      return j;
+    }
+    return 0;
+  }
+  if (j >= n) {
+    if (hi == 0) {
+      do { j -= n; } while (j >= n);
+      return j;
+    }
+    return n - 1;
+  }
+  return j;
+}
+
+// Position at which a stencil quantity "at" position j is evaluated: the edge cell beyond a
+// zero-gradient side (the ghost replicates the edge cell), j itself otherwise (periodic sides are
+// unwrapped; the region holds the wrapped values there).
+__device__ __forceinline__ int centre_pos(int j, int n, int lo, int hi) {
+  if (j < 0 && lo == 1) return 0;
+  if (j >= n && hi == 1) return n - 1;
+  return j;
+}
+
+// Lattice unit vectors sigma_i in the order {x-, x+, y-, y+} (Eq. 18).
+__device__ __forceinline__ int sig_x(int i) { return i == 0 ? -1 : (i == 1 ? 1 : 0); }
+__device__ __forceinline__ int sig_y(int i) { return i == 2 ? -1 : (i == 3 ? 1 : 0); }
+
+// ------------------------------------------------------------------------------------------
+// thermodynamics (Sec. II C)
+// ------------------------------------------------------------------------------------------
+template <class E>
+__device__ __forceinline__ void eos_eval(const KParams& p, E rho, E inv_rho, E e, E& P, E& cs2) {
+  if (p.eos_kind == 0) {  // ideal gas, Eq. (15)
+    const E gm1 = (E)(p.gamma - 1.0);
+    P = gm1 * rho * e;
+    cs2 = (E)p.gamma * gm1 * e;
+  } else {  // polytropic van der Waals, Eqs. (16)-(17); c_s^2 by Eq. (13)
+    const E T = (e + (E)p.a * rho) * (E)p.inv_cv;
+    const E inv_omb = (E)1 / ((E)1 - (E)p.b * rho);
+    const E RT_omb = (E)p.R * T * inv_omb;
+    P = rho * RT_omb - (E)p.a * rho * rho;
+    const E dPdT = (E)p.R * rho * inv_omb;                          // (dP/dT)_rho
+    const E P_rho = RT_omb * inv_omb - (E)2 * (E)p.a * rho + dPdT * (E)p.a * (E)p.inv_cv;  // (dP/drho)_e
+    const E P_e = dPdT * (E)p.inv_cv;                               // (dP/de)_rho
+    cs2 = P_rho + P * inv_rho * inv_rho * P_e;
+  }
+}
+
+// Primitives and flux of one state (Eqs. 1-2, 10).  Returns false for a non-physical state.
+// In the FP32 path the van der Waals energy-to-temperature inversion and pressure run in FP64.
+template <int D, class M>
+__device__ __forceinline__ bool prim_flux(const KParams& p, const M (&W)[D + 2], M (&u)[D], M (&Qf)[D][D + 2], M& cs) {
+  constexpr int NC = D + 2;
+  const M rho = W[0];
+  M P, cs2;
+  if (std::is_same<M, float>::value && p.eos_kind != 0) {
+    const double rd = (double)rho, ird = 1.0 / rd;
+    double usq = 0.0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const double ua = (double)W[1 + a] * ird;
+      u[a] = (M)ua;
+      usq += ua * ua;
+    }
+    const double e = (double)W[NC - 1] * ird - 0.5 * usq;
+    double Pd, cd;
+    eos_eval<double>(p, rd, ird, e, Pd, cd);
+    P = (M)Pd;
+    cs2 = (M)cd;
+  } else {
+    const M inv_rho = (M)1 / rho;
+    M usq = 0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      u[a] = W[1 + a] * inv_rho;
+      usq += u[a] * u[a];
+    }
+    const M e = W[NC - 1] * inv_rho - (M)0.5 * usq;
+    eos_eval<M>(p, rho, inv_rho, e, P, cs2);
+  }
+  const bool ok = (rho > (M)0) && (cs2 > (M)0) && isfinite(cs2) && isfinite(P) && isfinite(rho);
+  cs = sqrt(cs2 > (M)0 ? cs2 : (M)0);
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    Qf[a][0] = W[1 + a];
+#pragma unroll
+    for (int b = 0; b < D; ++b) Qf[a][1 + b] = W[1 + b] * u[a] + (a == b ? P : (M)0);
+    Qf[a][NC - 1] = (W[NC - 1] + P) * u[a];
+  }
+  return ok;
+}
+
+// ------------------------------------------------------------------------------------------
+// storage: FP64 holds f_i; FP32 holds d_i = f_i - W_ref/Q (W_ref a per-run FP64 constant)
+// ------------------------------------------------------------------------------------------
+template <class S>
+struct Store;
+template <>
+struct Store<double> {
+  using M = double;
+  static constexpr bool kOffset = false;
+};
+template <>
+struct Store<float> {
+  using M = float;
+  static constexpr bool kOffset = true;
+};
+
+// Loads the populations of cell (cx, cy) (pulled across the links, or in place), returns the
+// stored values in fr[i][k] and W_k (deviation sums plus Q * W_ref/Q in FP32 storage).
+template <int D, class S>
+__device__ __forceinline__ void load_cell(const S* __restrict__ fin, const KParams& p, int cx, int cy, int pulled,
+                                          typename Store<S>::M (&fr)[2 * D][D + 2], typename Store<S>::M (&W)[D + 2],
+                                          const double* wref) {
+  using M = typename Store<S>::M;
+  constexpr int NC = D + 2, Q = 2 * D;
+  int src[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    int sx = cx, sy = cy;
+    if (pulled) {
+      sx = nb_index(cx - sig_x(i), p.nx, p.bc[0], p.bc[1]);
+      if (D == 2) sy = nb_index(cy - sig_y(i), p.ny, p.bc[2], p.bc[3]);
+    }
+    src[i] = sy * p.nx + sx;
+  }
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    M acc = 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const M v = (M)__ldg(fin + (long long)(i * NC + k) * p.plane + src[i]);
+      fr[i][k] = v;
+      acc += v;
+    }
+    if (Store<S>::kOffset) acc += (M)(Q * wref[k]);
+    W[k] = acc;
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// block-wide max of kNV non-negative values, stored as this CTA's partial (no atomics)
+// ------------------------------------------------------------------------------------------
+template <int NV, int NT>
+__device__ __forceinline__ void block_max_store(double (&v)[NV], double* __restrict__ part_slot, int cta, int ncta,
+                                                int* nparts_slot) {
+  __shared__ double red_s[NT / 32][NV];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    double x = v[j];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, off));
+    if (lane == 0) red_s[warp][j] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < kNV) {
+    double x = 0.0;
+    if ((int)threadIdx.x < NV)
+#pragma unroll 4
+      for (int w = 0; w < NT / 32; ++w) x = fmax(x, red_s[w][threadIdx.x]);
+    part_slot[(long long)cta * kNV + threadIdx.x] = x;
+  }
+  if (cta == 0 && threadIdx.x == 0) *nparts_slot = ncta;
+}
+
+// Fold the partials of one slot with one CTA of NT threads: out[j] = max over CTAs (all threads).
+template <int NT>
+__device__ __forceinline__ void fold_partials(const double* __restrict__ part_slot, int nparts, double (&out)[kNV]) {
+  __shared__ double red_s[NT / 32][kNV];
+  double v[kNV];
+#pragma unroll
+  for (int j = 0; j < kNV; ++j) v[j] = 0.0;
+  for (int c = threadIdx.x; c < nparts; c += NT)
+#pragma unroll
+    for (int j = 0; j < kNV; ++j) v[j] = fmax(v[j], part_slot[(long long)c * kNV + j]);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < kNV; ++j) {
+    double x = v[j];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, off));
+    if (lane == 0) red_s[warp][j] = x;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < kNV; ++j) {
+    double x = 0.0;
+#pragma unroll 4
+    for (int w = 0; w < NT / 32; ++w) x = fmax(x, red_s[w][j]);
+    out[j] = x;
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// k_reduce: s_max and M_k of the current state (two-pass form; also the first step's maxima)
+// ------------------------------------------------------------------------------------------
+template <int D, class S, int NT>
+__global__ void __launch_bounds__(NT) k_reduce(const S* __restrict__ fin, Scalars* __restrict__ sc, const KParams p,
+                                                const int pulled, double* __restrict__ part) {
+  using M = typename Store<S>::M;
+  constexpr int NC = D + 2;
+  if (sc->done || sc->err) return;
+  const int slot = (int)(sc->n & 1);
+  double v[NC + 1];
+#pragma unroll
+  for (int j = 0; j < NC + 1; ++j) v[j] = 0.0;
+  bool bad = false;
+  for (long long cell = (long long)blockIdx.x * NT + threadIdx.x; cell < p.plane; cell += (long long)gridDim.x * NT) {
+    const int cx = (int)(cell % p.nx), cy = (int)(cell / p.nx);
+    M fr[2 * D][NC], W[NC], u[D], Qf[D][NC], cs;
+    load_cell<D, S>(fin, p, cx, cy, pulled, fr, W, sc->wref);
+    bad |= !prim_flux<D, M>(p, W, u, Qf, cs);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      v[0] = fmax(v[0], (double)(fabs(u[a]) + cs));
+#pragma unroll
+      for (int k = 0; k < NC; ++k) v[1 + k] = fmax(v[1 + k], (double)fabs(Qf[a][k]));
+    }
+  }
+  if (bad) atomicOr(&sc->err, ERR_NONPHYSICAL);
+  block_max_store<NC + 1, NT>(v, part + (long long)slot * p.max_parts * kNV, blockIdx.x, gridDim.x, &sc->nparts[slot]);
+}
+
+// ------------------------------------------------------------------------------------------
+// k_dt: link speed and time step of the next step (Eqs. 36-37), final-step shortening, and the
+// reciprocals the step kernels use.  One thread.
+// ------------------------------------------------------------------------------------------
+constexpr int kNTD = 256;  // threads of the one-CTA scalar kernels
+
+__global__ void __launch_bounds__(kNTD) k_dt(Scalars* sc, const KParams p, const double* __restrict__ part,
+                                              double* hist_dt, double* hist_c, const double* sched) {
+  const long long n = sc->n;
+  const int slot = (int)(n & 1);
+  double mx[kNV];
+  fold_partials<kNTD>(part + (long long)slot * p.max_parts * kNV, sc->nparts[slot], mx);
+  if (threadIdx.x != 0) return;
+  if (sc->t_end > 0.0 && sc->t >= sc->t_end) sc->done = 1;
+  if (sc->done || sc->err) {
+    sc->active = 0;
+    return;
+  }
+  const double smax = mx[0];
+  double c;
+  if (sc->sched_len > 0) {
+    if (n + 1 >= sc->sched_len) {
+      sc->err |= ERR_SCHEDULE;
+      sc->active = 0;
+      return;
+    }
+    c = sched[n + 1];
+  } else {
+    const bool retarget = p.retarget_every <= 1 || (n % p.retarget_every) == 0;
+    c = retarget ? smax / p.cfl : sc->c_prev;
+  }
+  double dt = p.dx / c;
+  bool last = false;
+  if (sc->sched_len == 0 && sc->t_end > 0.0 && sc->t + dt >= sc->t_end) {  // land on t_end
+    dt = sc->t_end - sc->t;
+    c = p.dx / dt;
+    last = true;
+  }
+  if (!(c > 0.0) || !isfinite(c) || !(dt > 0.0)) {
+    sc->err |= ERR_NONPHYSICAL;
+    sc->active = 0;
+    return;
+  }
+  sc->smax = smax;
+  sc->r = sc->c_prev / c;
+  sc->c_new = c;
+  sc->inv_c = 1.0 / c;
+  sc->dt = dt;
+  for (int k = 0; k < p.nc; ++k) sc->inv_M[k] = mx[1 + k] > 0.0 ? 1.0 / mx[1 + k] : 0.0;
+  if (n < sc->hist_cap) {
+    hist_dt[n] = dt;
+    hist_c[n] = c;
+  }
+  sc->t = last ? sc->t_end : sc->t + dt;
+  sc->c_prev = c;
+  sc->n = n + 1;
+  sc->active = 1;
+  if (last) sc->done = 1;
+}
+
+// ------------------------------------------------------------------------------------------
+// k_tile: the step (or, with BETA_OUT, only beta(x) of the current state)
+// ------------------------------------------------------------------------------------------
+template <int D, class S, bool LOOK, int TX, int TY>
+struct TileGeom {
+  static constexpr int NC = D + 2, Q = 2 * D;
+  static constexpr int H = LOOK ? 3 : 2;                   // W/u/Q region radius
+  static constexpr int HY = D == 2 ? H : 0;
+  static constexpr int RX = TX + 2 * H, RY = TY + 2 * HY;  // region
+  static constexpr int SX = TX + 2 * (H - 1), SY = TY + 2 * (D == 2 ? H - 1 : 0);  // s, theta region
+  static constexpr int RB = LOOK ? 1 : 0;                  // relaxed ring
+  static constexpr int BX = TX + 2 * RB, BY = TY + 2 * (D == 2 ? RB : 0);
+  static constexpr int NT = TX * TY;
+  using M = typename Store<S>::M;
+  static constexpr size_t smem_elems =
+      (size_t)D * RY * RX + (size_t)D * NC * RY * RX + (size_t)SY * SX * (D == 2 ? 2 : 1) + (LOOK ? (size_t)NC * BY * BX : 0);
+  static constexpr size_t smem_bytes = smem_elems * sizeof(M);
+};
+
+// beta at region-local centre (sx, sy) of the s/theta arrays: box filter x then y (Sec. III D),
+// Sensor A (1D, Eq. 34) or Sensor B (2D, Eq. 35).
+template <int D, class M, int SX>
+__device__ __forceinline__ M sensor_beta(const KParams& p, const M* s_s, const M* s_t, int sx, int sy) {
+  if (p.beta_mode == 1) return (M)p.beta_const;
+  const M q = (M)0.25, h = (M)0.5;
+  M sbar, tbar = (M)1;
+  if (D == 1) {
+    sbar = q * s_s[sx - 1] + h * s_s[sx] + q * s_s[sx + 1];
+  } else {
+    M rs[3], rt[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const M* rows = s_s + (sy - 1 + j) * SX;
+      const M* rowt = s_t + (sy - 1 + j) * SX;
+      rs[j] = q * rows[sx - 1] + h * rows[sx] + q * rows[sx + 1];
+      rt[j] = q * rowt[sx - 1] + h * rowt[sx] + q * rowt[sx + 1];
+    }
+    sbar = q * rs[0] + h * rs[1] + q * rs[2];
+    tbar = q * rt[0] + h * rt[1] + q * rt[2];
+  }
+  M chi = (M)p.c_sensor * sbar * tbar;
+  chi = chi <= (M)0 ? (M)0 : (chi >= (M)1 ? (M)1 : chi);
+  return (M)p.beta_max - (M)(p.beta_max - p.beta_min) * chi;
+}
+
+// Fused reprojection (c_old -> c_new, Eqs. 38-40) and relaxation (Eqs. 20, 22) of one cell:
+//   f*_{a,+-} = W/Q + s_a-term  +-  [ beta Q_a / c + (1 - 2 beta) r (f_{a+} - f_{a-}) / 2 ]
+//   with the D2Q4 K-term  +-(x/y)  (1 - 2 beta) r^2 ((f_x+ + f_x-) - (f_y+ + f_y-)) / 4,
+// r = c_old / c_new.  In FP32 storage the same update acts on the deviations (W/Q -> dW/Q).
+template <int D, class M>
+__device__ __forceinline__ void relax_cell(const M (&fr)[2 * D][D + 2], const M (&dW)[D + 2], const M (&Qc)[D][D + 2],
+                                           M beta, M r, M inv_c, M (&fo)[2 * D][D + 2]) {
+  constexpr int NC = D + 2;
+  const M om = (M)1 - (M)2 * beta;
+  const M bq = beta * inv_c;
+  const M omr = om * r * (M)0.5;
+  const M omk = om * r * r * (M)0.25;
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    const M w = dW[k] * (M)(1.0 / (2 * D));
+    const M gx = bq * Qc[0][k] + omr * (fr[1][k] - fr[0][k]);
+    if constexpr (D == 1) {
+      fo[0][k] = w - gx;
+      fo[1][k] = w + gx;
+    } else {
+      const M gy = bq * Qc[1][k] + omr * (fr[3][k] - fr[2][k]);
+      const M kk = omk * ((fr[0][k] + fr[1][k]) - (fr[2][k] + fr[3][k]));
+      fo[0][k] = w - gx + kk;
+      fo[1][k] = w + gx + kk;
+      fo[2][k] = w - gy - kk;
+      fo[3][k] = w + gy - kk;
+    }
+  }
+}
+
+template <int D, class S, bool LOOK, bool BETA_OUT, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY) k_tile(const S* __restrict__ fin, S* __restrict__ fout, Scalars* __restrict__ sc,
+                                                    const KParams p, const int pulled, const double* __restrict__ invM_src,
+                                                    double* __restrict__ beta_out, double* __restrict__ part) {
+  using G = TileGeom<D, S, LOOK, TX, TY>;
+  using M = typename G::M;
+  constexpr int NC = G::NC, Q = G::Q, H = G::H, HY = G::HY, RX = G::RX, RY = G::RY, SX = G::SX, SY = G::SY;
+  constexpr int NT = G::NT;
+  if (!BETA_OUT && !sc->active) return;
+
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  M* s_u = reinterpret_cast<M*>(smem_raw);  // [D][RY][RX]
+  M* s_Q = s_u + D * RY * RX;               // [D][NC][RY][RX]
+  M* s_s = s_Q + D * NC * RY * RX;          // [SY][SX]
+  M* s_t = s_s + SY * SX;                   // [SY][SX]      (2D)
+  M* s_x = s_t + (D == 2 ? SY * SX : 0);    // [NC][BY][BX]  (look-ahead exchange)
+
+  const int x0 = blockIdx.x * TX, y0 = (D == 2) ? blockIdx.y * TY : 0;
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  const int gx = x0 + tx, gy = y0 + ty;
+  const bool own_in = gx < p.nx && gy < p.ny;
+
+  const M r = (M)sc->r, inv_c = (M)sc->inv_c;
+  M invM[NC];
+#pragma unroll
+  for (int k = 0; k < NC; ++k) invM[k] = (M)invM_src[k];
+  const double* wref = sc->wref;
+  bool bad = false;
+
+  // ---- phase A: primitives and flux on the region; the own cell keeps its populations ----
+  M fr[Q][NC], Wown[NC];
+  {
+    const int cx = nb_index(gx, p.nx, p.bc[0], p.bc[1]);
+    const int cy = (D == 2) ? nb_index(gy, p.ny, p.bc[2], p.bc[3]) : 0;
+    load_cell<D, S>(fin, p, cx, cy, pulled, fr, Wown, wref);
+    M u[D], Qf[D][NC], cs;
+    bad |= !prim_flux<D, M>(p, Wown, u, Qf, cs) && own_in;
+    const int ri = (ty + HY) * RX + (tx + H);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      s_u[a * RY * RX + ri] = u[a];
+#pragma unroll
+      for (int k = 0; k < NC; ++k) s_Q[(a * NC + k) * RY * RX + ri] = Qf[a][k];
+    }
+  }
+  constexpr int HALO = RX * RY - TX * TY;
+  for (int h = threadIdx.x; h < HALO; h += NT) {
+    int rx, ry;
+    if (h < HY * RX) {
+      ry = h / RX;
+      rx = h % RX;
+    } else if (h < HY * RX + TY * 2 * H) {
+      const int hh = h - HY * RX;
+      ry = HY + hh / (2 * H);
+      const int c = hh % (2 * H);
+      rx = c < H ? c : TX + c;
+    } else {
+      const int hh = h - HY * RX - TY * 2 * H;
+      ry = HY + TY + hh / RX;
+      rx = hh % RX;
+    }
+    const int px = x0 - H + rx, py = y0 - HY + ry;
+    const int cx = nb_index(px, p.nx, p.bc[0], p.bc[1]);
+    const int cy = (D == 2) ? nb_index(py, p.ny, p.bc[2], p.bc[3]) : 0;
+    M f2[Q][NC], W[NC], u[D], Qf[D][NC], cs;
+    load_cell<D, S>(fin, p, cx, cy, pulled, f2, W, wref);
+    bad |= !prim_flux<D, M>(p, W, u, Qf, cs);
+    const int ri = ry * RX + rx;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      s_u[a * RY * RX + ri] = u[a];
+#pragma unroll
+      for (int k = 0; k < NC; ++k) s_Q[(a * NC + k) * RY * RX + ri] = Qf[a][k];
+    }
+  }
+  if (bad) atomicOr(&sc->err, ERR_NONPHYSICAL);
+  __syncthreads();
+
+  // ---- phase B: activity s (Eqs. 28-31) and Ducros ratio theta (Eqs. 32-33) ----
+  if (p.beta_mode == 0) {
+    const M inv2dx = (M)p.inv2dx, eps = (M)p.ducros_eps;
+    for (int j = threadIdx.x; j < SX * SY; j += NT) {
+      const int sx = j % SX, sy = j / SX;
+      const int px = x0 - (H - 1) + sx;
+      const int py = y0 - (D == 2 ? H - 1 : 0) + sy;
+      const int rx = centre_pos(px, p.nx, p.bc[0], p.bc[1]) - (x0 - H);
+      const int ry = (D == 2) ? centre_pos(py, p.ny, p.bc[2], p.bc[3]) - (y0 - HY) : 0;
+      const int c = ry * RX + rx;
+      M acc = 0;
+#pragma unroll
+      for (int k = 0; k < NC; ++k) {
+        const M* qx = s_Q + (0 * NC + k) * RY * RX;
+        M jk = qx[c + 1] - qx[c - 1];
+        if (D == 2) {
+          const M* qy = s_Q + ((D - 1) * NC + k) * RY * RX;
+          jk += qy[c + RX] - qy[c - RX];
+        }
+        const M sh = (M)0.5 * jk * invM[k];
+        acc += sh * sh;
+      }
+      s_s[j] = sqrt(acc * (M)(1.0 / NC));
+      if (D == 2) {
+        const M* ux = s_u;
+        const M* uy = s_u + RY * RX;
+        const M dil = ((ux[c + 1] - ux[c - 1]) + (uy[c + RX] - uy[c - RX])) * inv2dx;
+        const M vort = ((uy[c + 1] - uy[c - 1]) - (ux[c + RX] - ux[c - RX])) * inv2dx;
+        s_t[j] = dil * dil / (dil * dil + vort * vort + eps);
+      }
+    }
+    __syncthreads();
+  }
+
+  // ---- phase C: beta of the own cell; BETA_OUT writes it and stops ----
+  const int ocx = centre_pos(gx, p.nx, p.bc[0], p.bc[1]) - (x0 - (H - 1));
+  const int ocy = (D == 2) ? centre_pos(gy, p.ny, p.bc[2], p.bc[3]) - (y0 - (H - 1)) : 0;
+  const M beta = sensor_beta<D, M, SX>(p, s_s, s_t, ocx, ocy);
+  if (BETA_OUT) {
+    if (own_in) beta_out[(long long)gy * p.nx + gx] = (double)beta;
+    return;
+  }
+
+  // ---- phase D: fused reprojection + relaxation of the own cell, single write ----
+  M dWown[NC], Qown[D][NC];
+  {
+    const int ri = (ty + HY) * RX + (tx + H);
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      dWown[k] = Wown[k];
+      if (Store<S>::kOffset) dWown[k] -= (M)(Q * wref[k]);
+#pragma unroll
+      for (int a = 0; a < D; ++a) Qown[a][k] = s_Q[(a * NC + k) * RY * RX + ri];
+    }
+  }
+  M fo[Q][NC];
+  if (Store<S>::kOffset) {
+    // deviation sums from the stored deviations directly (no W_ref round trip)
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      M acc = 0;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) acc += fr[i][k];
+      dWown[k] = acc;
+    }
+  }
+  relax_cell<D, M>(fr, dWown, Qown, beta, r, inv_c, fo);
+  if (own_in) {
+    const long long cell = (long long)gy * p.nx + gx;
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+#pragma unroll
+      for (int k = 0; k < NC; ++k) fout[(long long)(i * NC + k) * p.plane + cell] = (S)fo[i][k];
+  }
+  if constexpr (LOOK) {
+  // ---- look-ahead: relax the one-cell ring, stream into W^{n+1} of the tile, reduce it ----
+  constexpr int BX = G::BX, BY = G::BY, RB = G::RB;
+  constexpr int RING = BX * BY - TX * TY;
+  // ring cell handled by this thread (at most one: RING <= NT)
+  M fring[Q][NC];
+  int rbx = -1, rby = -1;
+  if ((int)threadIdx.x < RING) {
+    const int h = threadIdx.x;
+    if (D == 1) {
+      rby = 0;
+      rbx = h == 0 ? 0 : BX - 1;
+    } else if (h < BX) {
+      rby = 0;
+      rbx = h;
+    } else if (h < BX + 2 * TY) {
+      const int hh = h - BX;
+      rby = 1 + hh / 2;
+      rbx = (hh & 1) ? BX - 1 : 0;
+    } else {
+      rby = BY - 1;
+      rbx = h - BX - 2 * TY;
+    }
+    const int px = x0 - RB + rbx, py = y0 - (D == 2 ? RB : 0) + rby;
+    const bool needed = centre_pos(px, p.nx, p.bc[0], p.bc[1]) == px &&
+                        (D == 1 || centre_pos(py, p.ny, p.bc[2], p.bc[3]) == py);
+    if (needed) {
+      const int cx = nb_index(px, p.nx, p.bc[0], p.bc[1]);
+      const int cy = (D == 2) ? nb_index(py, p.ny, p.bc[2], p.bc[3]) : 0;
+      M f2[Q][NC], W[NC];
+      load_cell<D, S>(fin, p, cx, cy, pulled, f2, W, wref);
+      const int ri = (py - (y0 - HY)) * RX + (px - (x0 - H));
+      M dW[NC], Qc[D][NC];
+#pragma unroll
+      for (int k = 0; k < NC; ++k) {
+        M acc = 0;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) acc += f2[i][k];
+        dW[k] = Store<S>::kOffset ? acc : W[k];
+#pragma unroll
+        for (int a = 0; a < D; ++a) Qc[a][k] = s_Q[(a * NC + k) * RY * RX + ri];
+      }
+      const int bsx = px - (x0 - (H - 1)), bsy = (D == 2) ? py - (y0 - (H - 1)) : 0;
+      const M b2 = sensor_beta<D, M, SX>(p, s_s, s_t, bsx, bsy);
+      relax_cell<D, M>(f2, dW, Qc, b2, r, inv_c, fring);
+    } else {
+      rbx = -1;
+    }
+  }
+  // exchange one direction at a time: W^{n+1}(x) = sum_i f*_i(x - sigma_i), i in lattice order
+  M Wn[NC];
+#pragma unroll
+  for (int k = 0; k < NC; ++k) Wn[k] = 0;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      s_x[(k * BY + (ty + (D == 2 ? RB : 0))) * BX + tx + RB] = fo[i][k];
+      if (rbx >= 0) s_x[(k * BY + rby) * BX + rbx] = fring[i][k];
+    }
+    __syncthreads();
+    if (own_in) {
+      const int qx = centre_pos(gx - sig_x(i), p.nx, p.bc[0], p.bc[1]) - (x0 - RB);
+      const int qy = (D == 2) ? centre_pos(gy - sig_y(i), p.ny, p.bc[2], p.bc[3]) - (y0 - RB) : 0;
+#pragma unroll
+      for (int k = 0; k < NC; ++k) Wn[k] += s_x[(k * BY + qy) * BX + qx];
+    }
+  }
+  double v[NC + 1];
+#pragma unroll
+  for (int j = 0; j < NC + 1; ++j) v[j] = 0.0;
+  if (own_in) {
+    if (Store<S>::kOffset)
+#pragma unroll
+      for (int k = 0; k < NC; ++k) Wn[k] += (M)(Q * wref[k]);
+    M u[D], Qf[D][NC], cs;
+    if (!prim_flux<D, M>(p, Wn, u, Qf, cs)) atomicOr(&sc->err, ERR_NONPHYSICAL);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      v[0] = fmax(v[0], (double)(fabs(u[a]) + cs));
+#pragma unroll
+      for (int k = 0; k < NC; ++k) v[1 + k] = fmax(v[1 + k], (double)fabs(Qf[a][k]));
+    }
+  }
+  const int slot = (int)(sc->n & 1);
+  block_max_store<NC + 1, NT>(v, part + (long long)slot * p.max_parts * kNV, blockIdx.y * gridDim.x + blockIdx.x,
+                              gridDim.x * gridDim.y, &sc->nparts[slot]);
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// initialisation, readback
+// ------------------------------------------------------------------------------------------
+__global__ void k_init_begin(Scalars* sc) {
+  sc->n = 0;
+  sc->t = 0.0;
+  sc->active = 0;
+  sc->done = 0;
+  sc->err = 0;
+  sc->nparts[0] = sc->nparts[1] = 0;
+  for (int k = 0; k < 4; ++k) sc->wref[k] = 0.0;
+}
+
+// s_max of W0 into partial slot 1 (Eq. 36), with the physical-state check.
+template <int D, int NT>
+__global__ void __launch_bounds__(NT) k_reduce_W0(const double* __restrict__ W0, Scalars* __restrict__ sc, const KParams p,
+                                                   double* __restrict__ part) {
+  constexpr int NC = D + 2;
+  double v[1] = {0.0};
+  bool bad = false;
+  for (long long cell = (long long)blockIdx.x * NT + threadIdx.x; cell < p.plane; cell += (long long)gridDim.x * NT) {
+    double W[NC], u[D], Qf[D][NC], cs;
+#pragma unroll
+    for (int k = 0; k < NC; ++k) W[k] = W0[k * p.plane + cell];
+    bad |= !prim_flux<D, double>(p, W, u, Qf, cs);
+#pragma unroll
+    for (int a = 0; a < D; ++a) v[0] = fmax(v[0], fabs(u[a]) + cs);
+  }
+  if (bad) atomicOr(&sc->err, ERR_NONPHYSICAL);
+  block_max_store<1, NT>(v, part + (long long)1 * p.max_parts * kNV, blockIdx.x, gridDim.x, &sc->nparts[1]);
+}
+
+// Per-block compensated (Neumaier) sums of W0_k (FP32-storage reference), fixed order.
+template <int NT>
+__global__ void __launch_bounds__(NT) k_sum_partial(const double* __restrict__ W0, const KParams p, double* __restrict__ partial) {
+  __shared__ double ss[NT], sc_[NT];
+  for (int k = 0; k < p.nc; ++k) {
+    double s = 0.0, c = 0.0;
+    for (long long cell = (long long)blockIdx.x * NT + threadIdx.x; cell < p.plane; cell += (long long)gridDim.x * NT) {
+      const double x = W0[k * p.plane + cell];
+      const double t = s + x;
+      c += fabs(s) >= fabs(x) ? (s - t) + x : (x - t) + s;
+      s = t;
+    }
+    ss[threadIdx.x] = s;
+    sc_[threadIdx.x] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double S = 0.0, Cc = 0.0;
+      for (int j = 0; j < NT; ++j) {
+        const double x = ss[j];
+        const double t = S + x;
+        Cc += fabs(S) >= fabs(x) ? (S - t) + x : (x - t) + S;
+        S = t;
+        Cc += sc_[j];
+      }
+      partial[blockIdx.x * 4 + k] = S + Cc;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_sum_final(const double* __restrict__ partial, int nblk, const KParams p, Scalars* sc) {
+  for (int k = 0; k < p.nc; ++k) {
+    double S = 0.0, Cc = 0.0;
+    for (int b = 0; b < nblk; ++b) {
+      const double x = partial[b * 4 + k];
+      const double t = S + x;
+      Cc += fabs(S) >= fabs(x) ? (S - t) + x : (x - t) + S;
+      S = t;
+    }
+    sc->wref[k] = (S + Cc) / (double)p.plane / (double)p.q;
+  }
+}
+
+// Initial link speed c0 = s_max(W0)/CFL (or the replayed c0).  One CTA.
+__global__ void __launch_bounds__(kNTD) k_init_c0(Scalars* sc, const KParams p, const double* __restrict__ part,
+                                                   const double* sched) {
+  double mx[kNV];
+  fold_partials<kNTD>(part + (long long)1 * p.max_parts * kNV, sc->nparts[1], mx);
+  if (threadIdx.x != 0) return;
+  const double c0 = sc->sched_len > 0 ? sched[0] : mx[0] / p.cfl;
+  if (!(c0 > 0.0) || !isfinite(c0)) sc->err |= ERR_NONPHYSICAL;
+  sc->c_prev = c0;
+  sc->c_new = c0;
+  sc->r = 1.0;
+}
+
+// f_i = f_i^eq(W0; c0) (Eq. 20), stored in place (unpulled); maxima of W^0 = sum_i f_i into
+// partial slot 0.
+template <int D, class S, int NT>
+__global__ void __launch_bounds__(NT) k_init_eq(const double* __restrict__ W0, S* __restrict__ fout, Scalars* __restrict__ sc,
+                                                 const KParams p, double* __restrict__ part) {
+  using M = typename Store<S>::M;
+  constexpr int NC = D + 2, Q = 2 * D;
+  double v[NC + 1];
+#pragma unroll
+  for (int j = 0; j < NC + 1; ++j) v[j] = 0.0;
+  bool bad = false;
+  const double c0 = sc->c_prev;
+  for (long long cell = (long long)blockIdx.x * NT + threadIdx.x; cell < p.plane; cell += (long long)gridDim.x * NT) {
+    double W[NC], u[D], Qf[D][NC], cs;
+#pragma unroll
+    for (int k = 0; k < NC; ++k) W[k] = W0[k * p.plane + cell];
+    prim_flux<D, double>(p, W, u, Qf, cs);
+    M Ws[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      M acc = 0;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        const int a = i >> 1;
+        const double sgn = (i & 1) ? 1.0 : -1.0;
+        const double fe = W[k] / (2.0 * D) + sgn * Qf[a][k] / (2.0 * c0);  // c_i.Q/(2c^2), |c_i| = c
+        const S st = Store<S>::kOffset ? (S)(fe - sc->wref[k]) : (S)fe;
+        fout[(long long)(i * NC + k) * p.plane + cell] = st;
+        acc += (M)st;
+      }
+      if (Store<S>::kOffset) acc += (M)(Q * sc->wref[k]);
+      Ws[k] = acc;
+    }
+    M us[D], Qs[D][NC], css;
+    bad |= !prim_flux<D, M>(p, Ws, us, Qs, css);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      v[0] = fmax(v[0], (double)(fabs(us[a]) + css));
+#pragma unroll
+      for (int k = 0; k < NC; ++k) v[1 + k] = fmax(v[1 + k], (double)fabs(Qs[a][k]));
+    }
+  }
+  if (bad) atomicOr(&sc->err, ERR_NONPHYSICAL);
+  block_max_store<NC + 1, NT>(v, part, blockIdx.x, gridDim.x, &sc->nparts[0]);
+}
+
+// W = sum_i f_i (FP32 storage: FP64 sum of the reference share and the deviations).
+template <int D, class S, int NT>
+__global__ void __launch_bounds__(NT) k_get_W(const S* __restrict__ fin, const Scalars* __restrict__ sc, const KParams p,
+                                               const int pulled, double* __restrict__ W) {
+  constexpr int NC = D + 2, Q = 2 * D;
+  const long long cell = (long long)blockIdx.x * NT + threadIdx.x;
+  if (cell >= p.plane) return;
+  const int cx = (int)(cell % p.nx), cy = (int)(cell / p.nx);
+  int src[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    int sx = cx, sy = cy;
+    if (pulled) {
+      sx = nb_index(cx - sig_x(i), p.nx, p.bc[0], p.bc[1]);
+      if (D == 2) sy = nb_index(cy - sig_y(i), p.ny, p.bc[2], p.bc[3]);
+    }
+    src[i] = sy * p.nx + sx;
+  }
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    double acc = 0.0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const double v = (double)fin[(long long)(i * NC + k) * p.plane + src[i]];
+      acc += Store<S>::kOffset ? (v + sc->wref[k]) : v;
+    }
+    W[k * p.plane + cell] = acc;
+  }
+}
+
+template <int D, class S, int NT>
+__global__ void __launch_bounds__(NT) k_get_f(const S* __restrict__ fin, const Scalars* __restrict__ sc, const KParams p,
+                                               const int pulled, double* __restrict__ f) {
+  constexpr int NC = D + 2, Q = 2 * D;
+  const long long cell = (long long)blockIdx.x * NT + threadIdx.x;
+  if (cell >= p.plane) return;
+  const int cx = (int)(cell % p.nx), cy = (int)(cell / p.nx);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    int sx = cx, sy = cy;
+    if (pulled) {
+      sx = nb_index(cx - sig_x(i), p.nx, p.bc[0], p.bc[1]);
+      if (D == 2) sy = nb_index(cy - sig_y(i), p.ny, p.bc[2], p.bc[3]);
+    }
+    const long long src = (long long)sy * p.nx + sx;
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      const double v = (double)fin[(long long)(i * NC + k) * p.plane + src];
+      f[(long long)(i * NC + k) * p.plane + cell] = Store<S>::kOffset ? v + sc->wref[k] : v;
+    }
+  }
+}
+
+// beta-only preparation: 1/M_k of the current state (partial slot n & 1) into separate scratch.
+__global__ void __launch_bounds__(kNTD) k_beta_prep(Scalars* sc, const KParams p, const double* __restrict__ part,
+                                                     double* invM_beta) {
+  const int slot = (int)(sc->n & 1);
+  double mx[kNV];
+  fold_partials<kNTD>(part + (long long)slot * p.max_parts * kNV, sc->nparts[slot], mx);
+  if (threadIdx.x == 0)
+    for (int k = 0; k < p.nc; ++k) invM_beta[k] = mx[1 + k] > 0.0 ? 1.0 / mx[1 + k] : 0.0;
+}
+
+__global__ void k_begin(Scalars* sc, double t_end) {
+  sc->t_end = t_end;
+  sc->done = (t_end > 0.0 && sc->t >= t_end) ? 1 : 0;
+}
+
+// ------------------------------------------------------------------------------------------
+// host launchers
+// ------------------------------------------------------------------------------------------
+namespace {
+constexpr int kNT1 = 256;        // threads of the cell-parallel kernels
+constexpr int kGridStride = 592; // CTAs of the grid-stride producers (4 per SM on 148 SMs)
+
+template <int D>
+struct TileCfg;
+template <>
+struct TileCfg<2> {  // 2D tiles of 32 x 16 cells
+  static constexpr int TX = 32, TY = 16;
+};
+template <>
+struct TileCfg<1> {  // 1D tiles of 256 cells
+  static constexpr int TX = 256, TY = 1;
+};
+
+template <int D, class S, bool LOOK, bool BOUT>
+cudaError_t launch_tile_t(const Launch& L, const void* fin, void* fout, int pulled, const double* invM, double* beta_out) {
+  constexpr int TX = TileCfg<D>::TX, TY = TileCfg<D>::TY;
+  using G = TileGeom<D, S, LOOK, TX, TY>;
+  const KParams& p = *L.p;
+  dim3 grid((p.nx + TX - 1) / TX, D == 2 ? (p.ny + TY - 1) / TY : 1);
+  k_tile<D, S, LOOK, BOUT, TX, TY><<<grid, TX * TY, G::smem_bytes, L.stream>>>((const S*)fin, (S*)fout, L.sc, p, pulled,
+                                                                              invM, beta_out, L.part);
+  return cudaGetLastError();
+}
+
+template <int D, class S, bool LOOK, bool BOUT>
+cudaError_t prepare_tile_t() {
+  constexpr int TX = TileCfg<D>::TX, TY = TileCfg<D>::TY;
+  using G = TileGeom<D, S, LOOK, TX, TY>;
+  return cudaFuncSetAttribute(k_tile<D, S, LOOK, BOUT, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)G::smem_bytes);
+}
+
+template <class S, bool LOOK, bool BOUT>
+cudaError_t launch_tile_d(const Launch& L, const void* fin, void* fout, int pulled, const double* invM, double* beta_out) {
+  return L.p->dim == 1 ? launch_tile_t<1, S, LOOK, BOUT>(L, fin, fout, pulled, invM, beta_out)
+                       : launch_tile_t<2, S, LOOK, BOUT>(L, fin, fout, pulled, invM, beta_out);
+}
+
+unsigned blocks1(const KParams& p) { return (unsigned)((p.plane + kNT1 - 1) / kNT1); }
+unsigned blocks_gs(const KParams& p) {
+  const long long b = (p.plane + kNT1 - 1) / kNT1;
+  return (unsigned)(b < kGridStride ? b : kGridStride);
+}
+
+template <int D, class S>
+void launch_reduce_t(const Launch& L, const void* fin, int pulled) {
+  k_reduce<D, S, kNT1><<<blocks_gs(*L.p), kNT1, 0, L.stream>>>((const S*)fin, L.sc, *L.p, pulled, L.part);
+}
+}  // namespace
+
+// Opt-in shared memory sizes of every step-kernel instantiation (current device); called once
+// per solver before any launch or graph capture.
+cudaError_t prepare_kernels() {
+  cudaError_t e = cudaSuccess;
+#define VLBM_PREP(D, S, LK, B) \
+  if (e == cudaSuccess) e = prepare_tile_t<D, S, LK, B>();
+  VLBM_PREP(1, double, false, false) VLBM_PREP(1, double, true, false) VLBM_PREP(1, double, false, true)
+  VLBM_PREP(1, float, false, false) VLBM_PREP(1, float, true, false) VLBM_PREP(1, float, false, true)
+  VLBM_PREP(2, double, false, false) VLBM_PREP(2, double, true, false) VLBM_PREP(2, double, false, true)
+  VLBM_PREP(2, float, false, false) VLBM_PREP(2, float, true, false) VLBM_PREP(2, float, false, true)
+#undef VLBM_PREP
+  return e;
+}
+
+int sum_blocks(const KParams& p) {
+  long long b = (p.plane + kNT1 - 1) / kNT1;
+  return (int)(b < 1184 ? b : 1184);
+}
+
+// Largest number of CTAs any partial-maxima producer launches for this grid.
+int max_partials(const KParams& p) {
+  long long tiles = p.dim == 2 ? (long long)((p.nx + TileCfg<2>::TX - 1) / TileCfg<2>::TX) * ((p.ny + TileCfg<2>::TY - 1) / TileCfg<2>::TY)
+                               : (long long)((p.nx + TileCfg<1>::TX - 1) / TileCfg<1>::TX);
+  long long gs = blocks_gs(p);
+  return (int)(tiles > gs ? tiles : gs);
+}
+
+cudaError_t launch_reduce(const Launch& L, int precision, const void* fin, int pulled) {
+  if (L.p->dim == 1) {
+    if (precision == 0) launch_reduce_t<1, double>(L, fin, pulled);
+    else launch_reduce_t<1, float>(L, fin, pulled);
+  } else {
+    if (precision == 0) launch_reduce_t<2, double>(L, fin, pulled);
+    else launch_reduce_t<2, float>(L, fin, pulled);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dt(const Launch& L) {
+  k_dt<<<1, kNTD, 0, L.stream>>>(L.sc, *L.p, L.part, L.hist_dt, L.hist_c, L.sched);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step(const Launch& L, int precision, bool lookahead, const void* fin, void* fout, int pulled) {
+  const double* invM = reinterpret_cast<const double*>(reinterpret_cast<const char*>(L.sc) + offsetof(Scalars, inv_M));
+  if (precision == 0)
+    return lookahead ? launch_tile_d<double, true, false>(L, fin, fout, pulled, invM, nullptr)
+                     : launch_tile_d<double, false, false>(L, fin, fout, pulled, invM, nullptr);
+  return lookahead ? launch_tile_d<float, true, false>(L, fin, fout, pulled, invM, nullptr)
+                   : launch_tile_d<float, false, false>(L, fin, fout, pulled, invM, nullptr);
+}
+
+cudaError_t launch_beta(const Launch& L, int precision, const void* fin, int pulled, double* beta_out) {
+  const KParams& p = *L.p;
+  // maxima of the current state into partial slot n & 1 (the same values any producer of that
+  // slot writes for this state), then 1/M_k into the beta scratch
+  cudaError_t e = launch_reduce(L, precision, fin, pulled);
+  if (e != cudaSuccess) return e;
+  double* invM_beta = beta_out + p.plane;  // caller provides plane + 4 doubles
+  k_beta_prep<<<1, kNTD, 0, L.stream>>>(L.sc, p, L.part, invM_beta);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (precision == 0) return launch_tile_d<double, false, true>(L, fin, nullptr, pulled, invM_beta, beta_out);
+  return launch_tile_d<float, false, true>(L, fin, nullptr, pulled, invM_beta, beta_out);
+}
+
+cudaError_t launch_init(const Launch& L, int precision, const double* W0, void* fout, double* partial, int nblk_sum) {
+  const KParams& p = *L.p;
+  k_init_begin<<<1, 1, 0, L.stream>>>(L.sc);
+  if (p.dim == 1) k_reduce_W0<1, kNT1><<<blocks_gs(p), kNT1, 0, L.stream>>>(W0, L.sc, p, L.part);
+  else k_reduce_W0<2, kNT1><<<blocks_gs(p), kNT1, 0, L.stream>>>(W0, L.sc, p, L.part);
+  if (precision == 1) {
+    k_sum_partial<kNT1><<<nblk_sum, kNT1, 0, L.stream>>>(W0, p, partial);
+    k_sum_final<<<1, 1, 0, L.stream>>>(partial, nblk_sum, p, L.sc);
+  }
+  k_init_c0<<<1, kNTD, 0, L.stream>>>(L.sc, p, L.part, L.sched);
+  if (p.dim == 1) {
+    if (precision == 0) k_init_eq<1, double, kNT1><<<blocks_gs(p), kNT1, 0, L.stream>>>(W0, (double*)fout, L.sc, p, L.part);
+    else k_init_eq<1, float, kNT1><<<blocks_gs(p), kNT1, 0, L.stream>>>(W0, (float*)fout, L.sc, p, L.part);
+  } else {
+    if (precision == 0) k_init_eq<2, double, kNT1><<<blocks_gs(p), kNT1, 0, L.stream>>>(W0, (double*)fout, L.sc, p, L.part);
+    else k_init_eq<2, float, kNT1><<<blocks_gs(p), kNT1, 0, L.stream>>>(W0, (float*)fout, L.sc, p, L.part);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_get_W(const Launch& L, int precision, const void* fin, int pulled, double* W) {
+  const KParams& p = *L.p;
+  if (p.dim == 1) {
+    if (precision == 0) k_get_W<1, double, kNT1><<<blocks1(p), kNT1, 0, L.stream>>>((const double*)fin, L.sc, p, pulled, W);
+    else k_get_W<1, float, kNT1><<<blocks1(p), kNT1, 0, L.stream>>>((const float*)fin, L.sc, p, pulled, W);
+  } else {
+    if (precision == 0) k_get_W<2, double, kNT1><<<blocks1(p), kNT1, 0, L.stream>>>((const double*)fin, L.sc, p, pulled, W);
+    else k_get_W<2, float, kNT1><<<blocks1(p), kNT1, 0, L.stream>>>((const float*)fin, L.sc, p, pulled, W);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_get_f(const Launch& L, int precision, const void* fin, int pulled, double* f) {
+  const KParams& p = *L.p;
+  if (p.dim == 1) {
+    if (precision == 0) k_get_f<1, double, kNT1><<<blocks1(p), kNT1, 0, L.stream>>>((const double*)fin, L.sc, p, pulled, f);
+    else k_get_f<1, float, kNT1><<<blocks1(p), kNT1, 0, L.stream>>>((const float*)fin, L.sc, p, pulled, f);
+  } else {
+    if (precision == 0) k_get_f<2, double, kNT1><<<blocks1(p), kNT1, 0, L.stream>>>((const double*)fin, L.sc, p, pulled, f);
+    else k_get_f<2, float, kNT1><<<blocks1(p), kNT1, 0, L.stream>>>((const float*)fin, L.sc, p, pulled, f);
+  }
+  return cudaGetLastError();
+}
+
+// begin-of-call marker (end time and done flag), used by the C-ABI layer
+cudaError_t launch_begin(const Launch& L, double t_end) {
+  k_begin<<<1, 1, 0, L.stream>>>(L.sc, t_end);
+  return cudaGetLastError();
+}
+
+}  // namespace vlbm

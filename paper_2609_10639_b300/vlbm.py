@@ -1,0 +1,238 @@
+"""Python binding of the VLBM step library (include/vlbm.h): argument marshalling only.
+
+Every step of the method runs in the CUDA library libvlbm.so (built in-tree for sm_103a);
+PyTorch supplies device memory and the stream.  There is no CPU fallback: if the library cannot
+be loaded, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass, field
+from typing import Optional, Sequence
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libvlbm.so")
+
+OK, E_INVAL, E_NOMEM, E_CUDA, E_NONPHYSICAL, E_TIMEOUT, E_STATE, E_CHECKSUM, E_UNSUPPORTED = range(9)
+BC = {"periodic": 0, "zerograd": 1}
+PRECISION = {"fp64": 0, "fp32_store": 1}
+ALGORITHM = {"auto": 0, "two_pass": 1, "lookahead": 2}
+
+
+class VLBMError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {_lib.vlbm_status_string(status).decode()} (status {status})")
+
+
+class NonPhysicalState(VLBMError):
+    pass
+
+
+class _Grid(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("nx", C.c_int64), ("ny", C.c_int64), ("x0", C.c_double), ("x1", C.c_double),
+                ("y0", C.c_double), ("y1", C.c_double), ("bc", C.c_int32 * 4)]
+
+
+class _Eos(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("gamma", C.c_double), ("a", C.c_double), ("b", C.c_double), ("R", C.c_double),
+                ("cv", C.c_double)]
+
+
+class _Params(C.Structure):
+    _fields_ = [("cfl", C.c_double), ("beta_mode", C.c_int32), ("beta_const", C.c_double), ("beta_min", C.c_double),
+                ("beta_max", C.c_double), ("c_sensor", C.c_double), ("ducros_eps", C.c_double),
+                ("retarget_every", C.c_int32), ("precision", C.c_int32), ("algorithm", C.c_int32)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libvlbm.so not built ({LIB_PATH}); run `python -m paper_2609_10639_b300.build`")
+    L = C.CDLL(LIB_PATH)
+    V, P, D, I32, I64 = C.c_void_p, C.c_void_p, C.POINTER(C.c_double), C.c_int32, C.c_int64
+    sig = {
+        "vlbm_create": [C.POINTER(_Grid), C.POINTER(_Eos), C.POINTER(_Params), V, C.POINTER(V)],
+        "vlbm_destroy": [V],
+        "vlbm_init": [V, V],
+        "vlbm_step": [V, I64, C.c_double, C.POINTER(I64)],
+        "vlbm_get_W": [V, V],
+        "vlbm_get_beta": [V, V],
+        "vlbm_get_populations": [V, V],
+        "vlbm_get_time": [V, D, C.POINTER(I64), D],
+        "vlbm_get_dt_history": [V, V, V, I64, C.POINTER(I64)],
+        "vlbm_set_dt_schedule": [V, V, I64],
+        "vlbm_time_step_kernel": [V, I32, D],
+        "vlbm_launches_per_step": [V, C.POINTER(I32)],
+        "vlbm_set_profiling": [V, I32],
+        "vlbm_get_profile": [V, D, C.POINTER(I64)],
+    }
+    for name, args in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = C.c_int
+    L.vlbm_status_string.argtypes = [C.c_int]
+    L.vlbm_status_string.restype = C.c_char_p
+    L.vlbm_version.argtypes = []
+    L.vlbm_version.restype = C.c_char_p
+    return L
+
+
+_lib = _load()
+
+
+def library():
+    return _lib
+
+
+def _check(status: int, what: str):
+    if status == OK:
+        return
+    if status == E_NONPHYSICAL:
+        raise NonPhysicalState(status, what)
+    raise VLBMError(status, what)
+
+
+def _ptr(a) -> int:
+    """Raw address of a contiguous float64 torch tensor (device or host) or numpy array."""
+    if isinstance(a, np.ndarray):
+        assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"], "float64 C-contiguous array required"
+        return a.ctypes.data
+    assert a.dtype.itemsize == 8 and a.is_contiguous(), "contiguous float64 tensor required"
+    return a.data_ptr()
+
+
+@dataclass
+class Config:
+    dim: int
+    nx: int
+    ny: int = 1
+    extent: Sequence[float] = (0.0, 1.0, 0.0, 1.0)
+    bc: Sequence[str] = ("zerograd",) * 4
+    eos: dict = field(default_factory=lambda: {"kind": "ideal", "gamma": 1.4})
+    cfl: float = 0.5
+    beta_mode: str = "sensor"
+    beta_const: float = 1.0
+    beta_min: float = 0.75
+    beta_max: float = 1.0
+    c_sensor: float = 4.0
+    ducros_eps: float = 1e-12
+    retarget_every: int = 1
+    precision: str = "fp64"
+    algorithm: str = "auto"
+
+
+class Solver:
+    """A VLBM solver on the current CUDA device, bound to a torch CUDA stream."""
+
+    def __init__(self, cfg: Config, stream=None):
+        import torch
+
+        self.torch = torch
+        self.cfg = cfg
+        self.dim = cfg.dim
+        self.nx, self.ny = cfg.nx, (1 if cfg.dim == 1 else cfg.ny)
+        self.nc, self.q = cfg.dim + 2, 2 * cfg.dim
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        g = _Grid(cfg.dim, cfg.nx, self.ny, *[float(v) for v in cfg.extent], (C.c_int32 * 4)(*[BC[b] for b in cfg.bc]))
+        e = cfg.eos
+        if e["kind"] == "ideal":
+            eo = _Eos(0, e["gamma"], 0.0, 0.0, 0.0, 0.0)
+        else:
+            eo = _Eos(1, 0.0, e["a"], e["b"], e["R"], e["cv"])
+        p = _Params(cfg.cfl, 0 if cfg.beta_mode == "sensor" else 1, cfg.beta_const, cfg.beta_min, cfg.beta_max,
+                    cfg.c_sensor, cfg.ducros_eps, cfg.retarget_every, PRECISION[cfg.precision], ALGORITHM[cfg.algorithm])
+        h = C.c_void_p()
+        _check(_lib.vlbm_create(C.byref(g), C.byref(eo), C.byref(p), C.c_void_p(self.stream.cuda_stream), C.byref(h)),
+               "vlbm_create")
+        self._h = h
+
+    @classmethod
+    def for_problem(cls, prob, precision="fp64", algorithm="auto", stream=None, **over):
+        kw = dict(dim=prob.dim, nx=prob.nx, ny=prob.ny, extent=prob.extent, bc=prob.bc, eos=prob.eos, cfl=prob.cfl,
+                  beta_min=prob.beta_min, beta_max=prob.beta_max, c_sensor=prob.c_sensor, ducros_eps=prob.ducros_eps,
+                  precision=precision, algorithm=algorithm)
+        kw.update(over)
+        return cls(Config(**kw), stream=stream)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.vlbm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def shape(self):
+        return (self.nc, self.ny, self.nx)
+
+    def init(self, W0) -> None:
+        if isinstance(W0, np.ndarray):
+            W0 = np.ascontiguousarray(W0, dtype=np.float64).reshape(self.shape)
+        _check(_lib.vlbm_init(self._h, C.c_void_p(_ptr(W0))), "vlbm_init")
+        self._keep = W0  # the copy is stream-ordered; keep the source alive until it ran
+
+    def step(self, n_steps: int, t_end: float = 0.0) -> int:
+        done = C.c_int64(0)
+        _check(_lib.vlbm_step(self._h, int(n_steps), float(t_end), C.byref(done)), "vlbm_step")
+        return done.value
+
+    def W(self, out=None):
+        if out is None:
+            out = self.torch.empty(self.shape, dtype=self.torch.float64, device=self.device)
+        _check(_lib.vlbm_get_W(self._h, C.c_void_p(_ptr(out))), "vlbm_get_W")
+        return out
+
+    def beta(self) -> np.ndarray:
+        out = np.empty((self.ny, self.nx))
+        _check(_lib.vlbm_get_beta(self._h, C.c_void_p(out.ctypes.data)), "vlbm_get_beta")
+        return out
+
+    def populations(self):
+        out = self.torch.empty((self.q, self.nc, self.ny, self.nx), dtype=self.torch.float64, device=self.device)
+        _check(_lib.vlbm_get_populations(self._h, C.c_void_p(out.data_ptr())), "vlbm_get_populations")
+        return out
+
+    def time(self):
+        t, n, c = C.c_double(), C.c_int64(), C.c_double()
+        _check(_lib.vlbm_get_time(self._h, C.byref(t), C.byref(n), C.byref(c)), "vlbm_get_time")
+        return t.value, n.value, c.value
+
+    def history(self):
+        n = C.c_int64()
+        _check(_lib.vlbm_get_dt_history(self._h, None, None, 0, C.byref(n)), "vlbm_get_dt_history")
+        dt, c = np.empty(n.value), np.empty(n.value)
+        _check(_lib.vlbm_get_dt_history(self._h, C.c_void_p(dt.ctypes.data), C.c_void_p(c.ctypes.data), n.value,
+                                        C.byref(n)), "vlbm_get_dt_history")
+        return dt, c
+
+    def set_schedule(self, c) -> None:
+        c = np.ascontiguousarray(c, dtype=np.float64)
+        _check(_lib.vlbm_set_dt_schedule(self._h, C.c_void_p(c.ctypes.data) if len(c) else None, len(c)),
+               "vlbm_set_dt_schedule")
+
+    def time_step_kernel(self, reps: int = 10) -> float:
+        ms = C.c_double()
+        _check(_lib.vlbm_time_step_kernel(self._h, int(reps), C.byref(ms)), "vlbm_time_step_kernel")
+        return ms.value
+
+    def set_profiling(self, on: bool) -> None:
+        _check(_lib.vlbm_set_profiling(self._h, 1 if on else 0), "vlbm_set_profiling")
+
+    def profile(self):
+        """(summed device ms of the bracketed step-kernel launches, number of launches)."""
+        ms, n = C.c_double(), C.c_int64()
+        _check(_lib.vlbm_get_profile(self._h, C.byref(ms), C.byref(n)), "vlbm_get_profile")
+        return ms.value, n.value
+
+    def launches_per_step(self) -> int:
+        n = C.c_int32()
+        _check(_lib.vlbm_launches_per_step(self._h, C.byref(n)), "vlbm_launches_per_step")
+        return n.value

@@ -148,10 +148,22 @@ def sod_1d(p: Problem = SOD_1D, left=(1.0, 0.0, 1.0), right=(0.125, 0.0, 0.1), x
     return conserved(p.eos, rho, [u], P)
 
 
-def quadrant_states(seed: int = 2):
+_QUAD_SEED_FILE = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "tests", "golden",
+                               "quadrant_seed.json")
+
+
+def quadrant_seed() -> int:
+    """Seed of the four-quadrant input: the first seed (from 2 up) whose states the oracle advances
+    to t = 0.25 on a 512 x 512 copy without leaving the physical states (stored beside the
+    fixture script that chose it)."""
+    with open(_QUAD_SEED_FILE) as fh:
+        return int(json.load(fh)["seed"])
+
+
+def quadrant_states(seed: Optional[int] = None):
     """Four (rho, u, v, P) states in NE, NW, SW, SE order; per state rho~U[0.1,2], u,v~U[-1,1],
     P~U[0.05,2], drawn in that order."""
-    g = SplitMix64(seed)
+    g = SplitMix64(quadrant_seed() if seed is None else seed)
     out = []
     for _ in range(4):
         rho = g.uniform(0.1, 2.0)
@@ -162,7 +174,7 @@ def quadrant_states(seed: int = 2):
     return out
 
 
-def quadrants_2d(p: Problem = QUADRANTS_2D, seed: int = 2, states=None) -> np.ndarray:
+def quadrants_2d(p: Problem = QUADRANTS_2D, seed: Optional[int] = None, states=None) -> np.ndarray:
     """Four-quadrant 2D Riemann problem with the discontinuities on x = 0.5 and y = 0.5."""
     st = states if states is not None else quadrant_states(seed)
     X, Y = cell_centres(p)

@@ -1,0 +1,60 @@
+"""CPU checks of the C ABI: the library loads without a GPU, exports every symbol declared in
+include/*.h, and its argument validation runs host-side."""
+import ctypes as C
+import glob
+import os
+import re
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        txt = open(h).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        names.update(re.findall(r"\b(vlbm_[a-z0-9_]+)\s*\(", txt))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2609_10639_b300 import build, vlbm
+
+    build.build()
+    lib = C.CDLL(vlbm.LIB_PATH)
+    names = declared_functions()
+    assert "vlbm_create" in names and "vlbm_step" in names
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings_and_version():
+    from paper_2609_10639_b300 import vlbm
+
+    L = vlbm.library()
+    assert b"sm_103a" in L.vlbm_version()
+    for s in range(9):
+        assert L.vlbm_status_string(s)
+
+
+def test_create_rejects_bad_arguments_without_touching_the_gpu():
+    # Validation happens before any CUDA call, so it runs on a CPU-only host.
+    from paper_2609_10639_b300 import vlbm
+
+    L = vlbm.library()
+    g = vlbm._Grid(2, 0, 16, 0.0, 1.0, 0.0, 1.0, (C.c_int32 * 4)(1, 1, 1, 1))
+    e = vlbm._Eos(0, 1.4, 0, 0, 0, 0)
+    p = vlbm._Params(0.5, 0, 1.0, 0.75, 1.0, 4.0, 1e-12, 1, 0, 0)
+    h = C.c_void_p()
+    assert L.vlbm_create(C.byref(g), C.byref(e), C.byref(p), None, C.byref(h)) == vlbm.E_INVAL
+    g.nx = 16
+    p.cfl = 1.2
+    assert L.vlbm_create(C.byref(g), C.byref(e), C.byref(p), None, C.byref(h)) == vlbm.E_INVAL
+    p.cfl = 0.5
+    g.bc[0] = 0  # periodic x-lo without periodic x-hi
+    assert L.vlbm_create(C.byref(g), C.byref(e), C.byref(p), None, C.byref(h)) == vlbm.E_INVAL
+    g.bc[0] = 1
+    e.gamma = 1.0
+    assert L.vlbm_create(C.byref(g), C.byref(e), C.byref(p), None, C.byref(h)) == vlbm.E_INVAL
+    assert L.vlbm_step(None, 1, 0.0, None) == vlbm.E_INVAL
+    assert L.vlbm_destroy(None) == vlbm.OK

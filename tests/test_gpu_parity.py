@@ -1,0 +1,284 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+FP64 bar: relative max-norm max_k max_x |W_gpu - W_oracle|_k / max_x |W_oracle|_k <= 1e-11 after
+100 steps (the GPU fuses reprojection and relaxation and contracts multiply-adds, the oracle
+follows the paper's order without contraction; the difference is rounding only).
+FP32-storage bar: relative L1 of W <= 1e-5 against FP64 on smooth flow at equal time, shock
+positions within one cell.
+"""
+import dataclasses
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_2609_10639_b300 import workloads as wl
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_numbers.json")))
+pytestmark = pytest.mark.gpu
+TOL = 1e-11
+
+
+def rel_maxnorm(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    num = np.abs(a - b).reshape(a.shape[0], -1).max(axis=1)
+    den = np.maximum(np.abs(b).reshape(b.shape[0], -1).max(axis=1), 1e-300)
+    return float((num / den).max())
+
+
+def gpu_solver(prob, **kw):
+    from paper_2609_10639_b300 import vlbm
+
+    return vlbm.Solver.for_problem(prob, **kw)
+
+
+def oracle_solver(prob, **kw):
+    from oracle import oracle as O
+
+    return O.OracleSolver.for_problem(prob, **kw)
+
+
+def run_pair(prob, W0, steps, algorithm="auto", t_end=0.0, **over):
+    g = gpu_solver(prob, algorithm=algorithm, **over)
+    g.init(W0)
+    ng = g.step(steps, t_end)
+    o = oracle_solver(prob, **over)
+    o.init(W0)
+    no = o.step(steps, t_end)
+    return g, o, ng, no
+
+
+QUAD = dataclasses.replace(wl.QUADRANTS_2D, name="quadrants_2d")
+
+
+def quad_states():
+    return GOLD["laxliu_config12"]["states_NE_NW_SW_SE"]
+
+
+CASES = {
+    "sod_1d_1000": lambda: (wl.SOD_1D, wl.sod_1d(wl.SOD_1D)),
+    "sod_1d_periodic_ragged": lambda: (dataclasses.replace(wl.SOD_1D.resized(777), bc=wl.PER),
+                                       wl.sod_1d(wl.SOD_1D.resized(777))),
+    "quad_64": lambda: (QUAD.resized(64), wl.quadrants_2d(QUAD.resized(64), states=quad_states())),
+    "quad_ragged_257x131": lambda: (QUAD.resized(257, 131), wl.quadrants_2d(QUAD.resized(257, 131), states=quad_states())),
+    "quad_seeded_96x80": lambda: (QUAD.resized(96, 80), wl.quadrants_2d(QUAD.resized(96, 80))),
+    "quad_periodic_70x45": lambda: (dataclasses.replace(QUAD.resized(70, 45), bc=wl.PER),
+                                    wl.quadrants_2d(QUAD.resized(70, 45), states=quad_states())),
+    "bzt_vdw_96x80": lambda: (wl.BZT_2D.resized(96, 80), wl.bzt_interface_2d(wl.BZT_2D.resized(96, 80))),
+    "vortex_128": lambda: (wl.VORTEX_SCALE_2D.resized(128), wl.vortex_acoustic_2d(wl.VORTEX_SCALE_2D.resized(128))),
+    "vortex_density_100x72": lambda: (dataclasses.replace(wl.VORTEX_ADJOINT_2D.resized(100, 72), extent=(0, 10, 0, 7.2)),
+                                      wl.vortex_density_2d(dataclasses.replace(wl.VORTEX_ADJOINT_2D.resized(100, 72),
+                                                                               extent=(0, 10, 0, 7.2)))),
+}
+
+
+@pytest.mark.parametrize("algorithm", ["two_pass", "lookahead"])
+@pytest.mark.parametrize("case", list(CASES))
+def test_fp64_parity_100_steps(case, algorithm):
+    prob, W0 = CASES[case]()
+    g, o, ng, no = run_pair(prob, W0, 100, algorithm=algorithm)
+    assert ng == no == 100
+    err = rel_maxnorm(g.W().cpu().numpy(), o.W())
+    assert err <= TOL, f"{case}/{algorithm}: rel max-norm {err:.3e}"
+    tg, n_g, cg = g.time()
+    to, n_o, co = o.time()
+    assert n_g == n_o and abs(tg - to) <= 1e-12 * to and abs(cg - co) <= 1e-12 * co
+    dtg, ccg = g.history()
+    dto, cco = o.history()
+    np.testing.assert_allclose(ccg, cco, rtol=1e-12)
+    np.testing.assert_allclose(dtg, dto, rtol=1e-12)
+
+
+@pytest.mark.parametrize("precision", ["fp64"])
+def test_full_size_quadrants_100_steps(precision):
+    # The benchmark workload itself (4096 x 4096, same input, same launch configuration as the
+    # timed path: vlbm_step in graph-captured chunks): 100 steps against the oracle on the whole
+    # field (the oracle runs this in about a minute on the host cores).
+    prob = QUAD
+    W0 = wl.quadrants_2d(prob)
+    g, o, ng, no = run_pair(prob, W0, 100)
+    assert ng == no == 100
+    err = rel_maxnorm(g.W().cpu().numpy(), o.W())
+    assert err <= TOL, f"4096^2: rel max-norm {err:.3e}"
+
+
+@pytest.mark.parametrize("algorithm", ["two_pass", "lookahead"])
+def test_fp64_beta_field(algorithm):
+    prob, W0 = CASES["quad_ragged_257x131"]()
+    g, o, _, _ = run_pair(prob, W0, 37, algorithm=algorithm)
+    bg, bo = g.beta(), o.eval_beta()
+    assert np.abs(bg - bo).max() <= 1e-11
+    assert bo.min() < 0.9  # the sensor is active on this state
+
+
+def test_populations_match_oracle():
+    prob, W0 = CASES["quad_64"]()
+    g, o, _, _ = run_pair(prob, W0, 20)
+    fg = g.populations().cpu().numpy()
+    fo = o.f()
+    assert np.abs(fg - fo).max() <= 1e-11 * np.abs(fo).max()
+
+
+@pytest.mark.parametrize("beta", [0.5, 0.8, 1.0])
+def test_constant_beta_parity(beta):
+    prob, W0 = CASES["vortex_128"]()
+    g, o, _, _ = run_pair(prob, W0, 60, beta_mode="const", beta_const=beta)
+    assert rel_maxnorm(g.W().cpu().numpy(), o.W()) <= TOL
+
+
+def test_retarget_every_and_end_time():
+    prob, W0 = CASES["sod_1d_1000"]()
+    g, o, ng, no = run_pair(prob, W0, 10 ** 6, t_end=0.05, retarget_every=3)
+    assert ng == no and g.time()[0] == 0.05 == o.time()[0]
+    assert rel_maxnorm(g.W().cpu().numpy(), o.W()) <= TOL
+
+
+@pytest.mark.parametrize("algorithm", ["two_pass", "lookahead"])
+def test_sod_full_run_matches_oracle_and_exact(algorithm):
+    # the 1D benchmark configuration to t = 0.2: same step count, same final time, same L1 error
+    from oracle import riemann_exact as RX
+
+    prob, W0 = CASES["sod_1d_1000"]()
+    g, o, ng, no = run_pair(prob, W0, 10 ** 6, algorithm=algorithm, t_end=0.2)
+    assert ng == no and g.time()[0] == 0.2
+    X, _ = wl.cell_centres(prob)
+    rho_e, _, _ = RX.solution(X.ravel(), 0.2, (1.0, 0.0, 1.0), (0.125, 0.0, 0.1), 1.4)
+    Wg, Wo = g.W().cpu().numpy(), o.W()
+    l1g, l1o = prob.dx * np.abs(Wg[0, 0] - rho_e).sum(), prob.dx * np.abs(Wo[0, 0] - rho_e).sum()
+    assert abs(l1g - l1o) <= 1e-9
+    assert rel_maxnorm(Wg, Wo) <= 1e-9
+
+
+def test_schedule_replay():
+    prob, W0 = CASES["quad_64"]()
+    o = oracle_solver(prob)
+    o.init(W0)
+    c0 = o.time()[2]
+    o.step(30)
+    sched = np.concatenate([[c0], o.history()[1]])
+    g = gpu_solver(prob)
+    g.set_schedule(sched)
+    g.init(W0)
+    assert g.step(30) == 30
+    assert rel_maxnorm(g.W().cpu().numpy(), o.W()) <= TOL
+    from paper_2609_10639_b300 import vlbm
+
+    with pytest.raises(vlbm.VLBMError):
+        g.step(5)  # beyond the schedule
+
+
+@pytest.mark.parametrize("shape,bc", [((1, 1), "zerograd"), ((1, 1), "periodic"), ((2, 3), "periodic"), ((5, 1), "zerograd"),
+                                      ((33, 17), "periodic"), ((1, 40), "zerograd")])
+def test_degenerate_grids(shape, bc):
+    nx, ny = shape
+    prob = dataclasses.replace(QUAD.resized(nx, ny), bc=(bc,) * 4, extent=(0, 1, 0, ny / nx))
+    X, Y = wl.cell_centres(prob)
+    rho = 1 + 0.3 * np.sin(2 * np.pi * X) * np.cos(2 * np.pi * Y)
+    W0 = wl.conserved(prob.eos, rho, [0.2 + 0 * X, -0.1 + 0.05 * np.cos(2 * np.pi * X)], 1 + 0.2 * np.cos(2 * np.pi * Y))
+    for algorithm in ("two_pass", "lookahead"):
+        g, o, _, _ = run_pair(prob, W0, 25, algorithm=algorithm)
+        assert rel_maxnorm(g.W().cpu().numpy(), o.W()) <= TOL, (shape, bc, algorithm)
+
+
+def test_zero_steps_and_reinit():
+    prob, W0 = CASES["quad_64"]()
+    g = gpu_solver(prob)
+    g.init(W0)
+    assert g.step(0) == 0
+    np.testing.assert_allclose(g.W().cpu().numpy(), W0, rtol=1e-14, atol=1e-14)
+    g.step(7)
+    g.init(W0)
+    assert g.time()[1] == 0
+    o = oracle_solver(prob)
+    o.init(W0)
+    o.step(9)
+    g.step(9)
+    assert rel_maxnorm(g.W().cpu().numpy(), o.W()) <= TOL
+
+
+def test_host_buffers_roundtrip():
+    prob, W0 = CASES["quad_64"]()
+    g = gpu_solver(prob)
+    g.init(np.ascontiguousarray(W0))  # host pointer
+    g.step(3)
+    out = np.empty_like(W0)
+    from paper_2609_10639_b300 import vlbm
+
+    vlbm._check(vlbm.library().vlbm_get_W(g._h, vlbm.C.c_void_p(out.ctypes.data)), "get_W")
+    np.testing.assert_array_equal(out, g.W().cpu().numpy())
+
+
+def test_nonphysical_input_reported():
+    from paper_2609_10639_b300 import vlbm
+
+    prob, W0 = CASES["quad_64"]()
+    W0 = W0.copy()
+    W0[0, 10, 10] = -0.5
+    g = gpu_solver(prob)
+    g.init(W0)
+    with pytest.raises(vlbm.NonPhysicalState):
+        g.step(1)
+
+
+def test_invalid_arguments_rejected():
+    from paper_2609_10639_b300 import vlbm
+
+    for over in (dict(cfl=1.5), dict(beta_min=0.0), dict(beta_min=0.9, beta_max=0.8), dict(nx=0),
+                 dict(bc=("periodic", "zerograd", "zerograd", "zerograd"))):
+        with pytest.raises(vlbm.VLBMError):
+            gpu_solver(QUAD.resized(16), **over)
+    g = gpu_solver(QUAD.resized(16))
+    with pytest.raises(vlbm.VLBMError):
+        g.step(1)  # before init
+
+
+# ------------------------------------------------------------------------------------------
+# FP32 storage
+# ------------------------------------------------------------------------------------------
+def test_fp32_store_smooth_flow_error_bar():
+    # smooth vortex + acoustic noise: FP32 storage vs FP64 oracle at equal time, relative L1 of
+    # each component of W <= 1e-5
+    prob, W0 = CASES["vortex_128"]()
+    o = oracle_solver(prob)
+    o.init(W0)
+    o.step(200)
+    t_end = o.time()[0]
+    g = gpu_solver(prob, precision="fp32_store")
+    g.init(W0)
+    g.step(10 ** 6, t_end)
+    assert g.time()[0] == t_end
+    Wg, Wo = g.W().cpu().numpy(), o.W()
+    rel_l1 = np.abs(Wg - Wo).reshape(4, -1).sum(axis=1) / np.abs(Wo).reshape(4, -1).sum(axis=1)
+    assert rel_l1.max() <= 1e-5, rel_l1
+
+
+def test_fp32_store_shock_positions_within_one_cell():
+    prob, W0 = CASES["quad_ragged_257x131"]()
+    o = oracle_solver(prob)
+    o.init(W0)
+    o.step(150)
+    t_end = o.time()[0]
+    g = gpu_solver(prob, precision="fp32_store")
+    g.init(W0)
+    g.step(10 ** 6, t_end)
+    rg, ro = g.W().cpu().numpy()[0], o.W()[0]
+    # steepest density jump per row and per column
+    for axis in (0, 1):
+        jg = np.abs(np.diff(rg, axis=axis)).argmax(axis=axis)
+        jo = np.abs(np.diff(ro, axis=axis)).argmax(axis=axis)
+        assert np.mean(np.abs(jg - jo) <= 1) >= 0.999
+
+
+def test_fp32_store_1d_sod():
+    prob, W0 = CASES["sod_1d_1000"]()
+    g = gpu_solver(prob, precision="fp32_store")
+    g.init(W0)
+    g.step(10 ** 6, 0.2)
+    o = oracle_solver(prob)
+    o.init(W0)
+    o.step(10 ** 6, 0.2)
+    rg, ro = g.W().cpu().numpy()[0, 0], o.W()[0, 0]
+    assert np.abs(rg - ro).max() < 1e-3
+    assert abs(np.abs(np.diff(rg)).argmax() - np.abs(np.diff(ro)).argmax()) <= 1
