@@ -229,7 +229,9 @@ vlbm_status vlbm_create(const vlbm_grid* grid, const vlbm_eos* eos, const vlbm_p
   if (!grid || !eos || !params || !out) return VLBM_E_INVAL;
   if (grid->dim != 1 && grid->dim != 2) return VLBM_E_INVAL;
   const long long nx = grid->nx, ny = grid->dim == 1 ? 1 : grid->ny;
-  if (nx < 1 || ny < 1 || nx > 2147483647LL || ny > 2147483647LL || nx * ny > 2147483647LL) return VLBM_E_INVAL;
+  // 32-bit population offsets: 2D (D+2) nx ny values per buffer must stay below 2^31
+  const long long nvals = 2LL * grid->dim * (grid->dim + 2);
+  if (nx < 1 || ny < 1 || nx > 2147483647LL || ny > 2147483647LL || nx * ny > 2147483647LL / nvals) return VLBM_E_INVAL;
   if (!(grid->x1 > grid->x0)) return VLBM_E_INVAL;
   for (int j = 0; j < 4; ++j)
     if (grid->bc[j] != VLBM_BC_PERIODIC && grid->bc[j] != VLBM_BC_ZEROGRAD) return VLBM_E_INVAL;
@@ -275,6 +277,38 @@ vlbm_status vlbm_create(const vlbm_grid* grid, const vlbm_eos* eos, const vlbm_p
   p.ducros_eps = params->ducros_eps;
   p.retarget_every = params->retarget_every;
   p.max_parts = vlbm::max_partials(p);
+  {
+    vlbm::Coef<double>& c = p.cd;
+    c.gamma = p.gamma;
+    c.gm1 = p.gamma - 1.0;
+    c.ggm1 = p.gamma * (p.gamma - 1.0);
+    c.a = p.a;
+    c.b = p.b;
+    c.R = p.R;
+    c.inv_cv = p.inv_cv;
+    c.a_inv_cv = p.a * p.inv_cv;
+    c.c_sensor = p.c_sensor;
+    c.beta_max = p.beta_max;
+    c.dbeta = p.beta_max - p.beta_min;
+    c.beta_const = p.beta_const;
+    c.inv2dx = p.inv2dx;
+    c.eps = p.ducros_eps;
+    vlbm::Coef<float>& f = p.cf;
+    f.gamma = (float)c.gamma;
+    f.gm1 = (float)c.gm1;
+    f.ggm1 = (float)c.ggm1;
+    f.a = (float)c.a;
+    f.b = (float)c.b;
+    f.R = (float)c.R;
+    f.inv_cv = (float)c.inv_cv;
+    f.a_inv_cv = (float)c.a_inv_cv;
+    f.c_sensor = (float)c.c_sensor;
+    f.beta_max = (float)c.beta_max;
+    f.dbeta = (float)c.dbeta;
+    f.beta_const = (float)c.beta_const;
+    f.inv2dx = (float)c.inv2dx;
+    f.eps = (float)c.eps;
+  }
   h->precision = params->precision;
   h->elem = params->precision == VLBM_FP64 ? 8 : 4;
   // Look-ahead (one pass over HBM per step) for FP32 storage, which is bandwidth-bound; the FP64

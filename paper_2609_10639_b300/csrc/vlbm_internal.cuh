@@ -19,6 +19,9 @@ struct Scalars {
   double inv_M[4];    // 1 / max_{x,alpha} |Q_alpha,k| of the step in flight (0 where the max is 0)
   double smax;        // s_max of the step in flight (Eq. 36)
   double wref[4];     // FP32 storage: W_ref_k / Q, the share subtracted from every population
+  float r_f, inv_c_f; // FP32 copies of r and 1/c_new (FP32-storage step)
+  float inv_M_f[4];   // FP32 copy of 1/M_k
+  float wq_f[4];      // FP32 storage: Q * W_ref_k / Q = W_ref_k as float
   long long n;        // steps completed once the step in flight has completed
   long long hist_cap; // capacity of the (dt, c) history arrays
   long long sched_len;// length of the replayed link-speed schedule (0: CFL rule)
@@ -36,6 +39,17 @@ constexpr int kNV = 5;
 
 enum { ERR_NONPHYSICAL = 1, ERR_SCHEDULE = 2 };
 
+// Coefficients of the step in the arithmetic type of a path (FP64, or FP32 for FP32 storage),
+// precomputed on the host so that no per-cell conversion runs on the FP64 pipe.
+template <class M>
+struct Coef {
+  M gamma, gm1, ggm1;           // gamma, gamma - 1, gamma (gamma - 1)          (Eq. 15)
+  M a, b, R, inv_cv, a_inv_cv;  // van der Waals a, b, R, 1/cv, a/cv         (Eqs. 16-17)
+  M c_sensor, beta_max, dbeta;  // C_sensor, beta_max, beta_max - beta_min   (Eqs. 34-35)
+  M beta_const;                 // constant-beta mode
+  M inv2dx, eps;                // 1/(2 dx), Ducros regulariser              (Eqs. 32-33)
+};
+
 // Constant per-solver parameters, passed to kernels by value.
 struct KParams {
   int dim, nc, q;
@@ -50,6 +64,8 @@ struct KParams {
   double beta_const, beta_min, beta_max, c_sensor, ducros_eps;
   int retarget_every;
   int max_parts;    // capacity of one partial-maxima slot (CTAs of the largest producer)
+  Coef<double> cd;
+  Coef<float> cf;
 };
 
 // Host-side launch helpers (defined in vlbm_kernels.cu).

@@ -67,30 +67,55 @@ __device__ __forceinline__ int centre_pos(int j, int n, int lo, int hi) {
 __device__ __forceinline__ int sig_x(int i) { return i == 0 ? -1 : (i == 1 ? 1 : 0); }
 __device__ __forceinline__ int sig_y(int i) { return i == 2 ? -1 : (i == 3 ? 1 : 0); }
 
+template <class M>
+__device__ __forceinline__ const Coef<M>& coef(const KParams& p);
+template <>
+__device__ __forceinline__ const Coef<double>& coef<double>(const KParams& p) { return p.cd; }
+template <>
+__device__ __forceinline__ const Coef<float>& coef<float>(const KParams& p) { return p.cf; }
+
+// Step scalars in the arithmetic type of a path (the FP32 copies are written by k_dt).
+template <class M>
+struct StepScalars;
+template <>
+struct StepScalars<double> {
+  static __device__ __forceinline__ double r(const Scalars* s) { return s->r; }
+  static __device__ __forceinline__ double inv_c(const Scalars* s) { return s->inv_c; }
+  static __device__ __forceinline__ const double* inv_M(const Scalars* s) { return s->inv_M; }
+  static __device__ __forceinline__ double wq(const Scalars* s, int k) { return 0.0; }
+};
+template <>
+struct StepScalars<float> {
+  static __device__ __forceinline__ float r(const Scalars* s) { return s->r_f; }
+  static __device__ __forceinline__ float inv_c(const Scalars* s) { return s->inv_c_f; }
+  static __device__ __forceinline__ const float* inv_M(const Scalars* s) { return s->inv_M_f; }
+  static __device__ __forceinline__ float wq(const Scalars* s, int k) { return s->wq_f[k]; }
+};
+
 // ------------------------------------------------------------------------------------------
 // thermodynamics (Sec. II C)
 // ------------------------------------------------------------------------------------------
 template <class E>
-__device__ __forceinline__ void eos_eval(const KParams& p, E rho, E inv_rho, E e, E& P, E& cs2) {
+__device__ __forceinline__ void eos_eval(const KParams& p, const Coef<E>& c, E rho, E inv_rho, E e, E& P, E& cs2) {
   if (p.eos_kind == 0) {  // ideal gas, Eq. (15)
-    const E gm1 = (E)(p.gamma - 1.0);
-    P = gm1 * rho * e;
-    cs2 = (E)p.gamma * gm1 * e;
+    P = c.gm1 * rho * e;
+    cs2 = c.ggm1 * e;
   } else {  // polytropic van der Waals, Eqs. (16)-(17); c_s^2 by Eq. (13)
-    const E T = (e + (E)p.a * rho) * (E)p.inv_cv;
-    const E inv_omb = (E)1 / ((E)1 - (E)p.b * rho);
-    const E RT_omb = (E)p.R * T * inv_omb;
-    P = rho * RT_omb - (E)p.a * rho * rho;
-    const E dPdT = (E)p.R * rho * inv_omb;                          // (dP/dT)_rho
-    const E P_rho = RT_omb * inv_omb - (E)2 * (E)p.a * rho + dPdT * (E)p.a * (E)p.inv_cv;  // (dP/drho)_e
-    const E P_e = dPdT * (E)p.inv_cv;                               // (dP/de)_rho
+    const E T = (e + c.a * rho) * c.inv_cv;
+    const E inv_omb = (E)1 / ((E)1 - c.b * rho);
+    const E RT_omb = c.R * T * inv_omb;
+    P = rho * RT_omb - c.a * rho * rho;
+    const E dPdT = c.R * rho * inv_omb;                                       // (dP/dT)_rho
+    const E P_rho = RT_omb * inv_omb - (E)2 * c.a * rho + dPdT * c.a_inv_cv;  // (dP/drho)_e
+    const E P_e = dPdT * c.inv_cv;                                            // (dP/de)_rho
     cs2 = P_rho + P * inv_rho * inv_rho * P_e;
   }
 }
 
-// Primitives and flux of one state (Eqs. 1-2, 10).  Returns false for a non-physical state.
-// In the FP32 path the van der Waals energy-to-temperature inversion and pressure run in FP64.
-template <int D, class M>
+// Primitives and flux of one state (Eqs. 1-2, 10); with NEED_CS also c_s and the physical-state
+// check (returns false for rho <= 0, c_s^2 <= 0 or non-finite values).  In the FP32 path the van
+// der Waals energy-to-temperature inversion and pressure run in FP64.
+template <int D, class M, bool NEED_CS>
 __device__ __forceinline__ bool prim_flux(const KParams& p, const M (&W)[D + 2], M (&u)[D], M (&Qf)[D][D + 2], M& cs) {
   constexpr int NC = D + 2;
   const M rho = W[0];
@@ -106,7 +131,7 @@ __device__ __forceinline__ bool prim_flux(const KParams& p, const M (&W)[D + 2],
     }
     const double e = (double)W[NC - 1] * ird - 0.5 * usq;
     double Pd, cd;
-    eos_eval<double>(p, rd, ird, e, Pd, cd);
+    eos_eval<double>(p, p.cd, rd, ird, e, Pd, cd);
     P = (M)Pd;
     cs2 = (M)cd;
   } else {
@@ -118,10 +143,13 @@ __device__ __forceinline__ bool prim_flux(const KParams& p, const M (&W)[D + 2],
       usq += u[a] * u[a];
     }
     const M e = W[NC - 1] * inv_rho - (M)0.5 * usq;
-    eos_eval<M>(p, rho, inv_rho, e, P, cs2);
+    eos_eval<M>(p, coef<M>(p), rho, inv_rho, e, P, cs2);
   }
-  const bool ok = (rho > (M)0) && (cs2 > (M)0) && isfinite(cs2) && isfinite(P) && isfinite(rho);
-  cs = sqrt(cs2 > (M)0 ? cs2 : (M)0);
+  bool ok = true;
+  if (NEED_CS) {
+    ok = (rho > (M)0) && (cs2 > (M)0) && isfinite(cs2) && isfinite(P);
+    cs = sqrt(cs2 > (M)0 ? cs2 : (M)0);
+  }
 #pragma unroll
   for (int a = 0; a < D; ++a) {
     Qf[a][0] = W[1 + a];
@@ -148,60 +176,105 @@ struct Store<float> {
   static constexpr bool kOffset = true;
 };
 
-// Loads the populations of cell (cx, cy) (pulled across the links, or in place), returns the
-// stored values in fr[i][k] and W_k (deviation sums plus Q * W_ref/Q in FP32 storage).
+// Loads the populations of cell (cx, cy), pulled across the links (or in place), into fr[i][k].
+// `interior`: the caller guarantees that (cx, cy) and its four neighbours lie inside the domain
+// (no boundary rule needed).  Offsets are 32-bit (vlbm_create bounds Q (D+2) nx ny below 2^31).
 template <int D, class S>
 __device__ __forceinline__ void load_cell(const S* __restrict__ fin, const KParams& p, int cx, int cy, int pulled,
-                                          typename Store<S>::M (&fr)[2 * D][D + 2], typename Store<S>::M (&W)[D + 2],
-                                          const double* wref) {
+                                          bool interior, typename Store<S>::M (&fr)[2 * D][D + 2]) {
   using M = typename Store<S>::M;
   constexpr int NC = D + 2, Q = 2 * D;
+  const int plane = (int)p.plane;
   int src[Q];
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     int sx = cx, sy = cy;
     if (pulled) {
-      sx = nb_index(cx - sig_x(i), p.nx, p.bc[0], p.bc[1]);
-      if (D == 2) sy = nb_index(cy - sig_y(i), p.ny, p.bc[2], p.bc[3]);
+      if (interior) {
+        sx = cx - sig_x(i);
+        sy = cy - sig_y(i);
+      } else {
+        sx = nb_index(cx - sig_x(i), p.nx, p.bc[0], p.bc[1]);
+        if (D == 2) sy = nb_index(cy - sig_y(i), p.ny, p.bc[2], p.bc[3]);
+      }
     }
     src[i] = sy * p.nx + sx;
   }
 #pragma unroll
-  for (int k = 0; k < NC; ++k) {
-    M acc = 0;
+  for (int k = 0; k < NC; ++k)
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const M v = (M)__ldg(fin + (long long)(i * NC + k) * p.plane + src[i]);
-      fr[i][k] = v;
-      acc += v;
-    }
-    if (Store<S>::kOffset) acc += (M)(Q * wref[k]);
+    for (int i = 0; i < Q; ++i) fr[i][k] = (M)__ldg(fin + ((i * NC + k) * plane + src[i]));
+}
+
+// Zeroth moment of one cell: W_k = sum_i f_i (direction pairs first); in FP32 storage the sum of
+// deviations plus Q W_ref/Q (wq).
+template <int D, class M, bool OFFSET>
+__device__ __forceinline__ void moments(const M (&fr)[2 * D][D + 2], const M* wq, M (&W)[D + 2]) {
+#pragma unroll
+  for (int k = 0; k < D + 2; ++k) {
+    M acc = fr[0][k] + fr[1][k];
+    if constexpr (D == 2) acc += fr[2][k] + fr[3][k];
+    if constexpr (OFFSET) acc += wq[k];
     W[k] = acc;
   }
 }
 
 // ------------------------------------------------------------------------------------------
-// block-wide max of kNV non-negative values, stored as this CTA's partial (no atomics)
+// Maxima: per-cell values reduced within a CTA and stored as the CTA's partial (no atomics).
+// FP64: non-negative doubles compared as their 64-bit patterns (same order, integer pipe);
+// FP32: float max.  The one-CTA link-speed kernel folds the partials.
 // ------------------------------------------------------------------------------------------
-template <int NV, int NT>
-__device__ __forceinline__ void block_max_store(double (&v)[NV], double* __restrict__ part_slot, int cta, int ncta,
-                                                int* nparts_slot) {
-  __shared__ double red_s[NT / 32][NV];
+template <class M>
+struct Red;
+template <>
+struct Red<double> {
+  using T = unsigned long long;
+  static __device__ __forceinline__ T make(double x) {  // |x| as an ordered bit pattern
+    return (T)__double_as_longlong(x) & 0x7fffffffffffffffull;
+  }
+  static __device__ __forceinline__ T mx(T a, T b) { return a > b ? a : b; }
+  static __device__ __forceinline__ double value(T v) { return __longlong_as_double((long long)v); }
+};
+template <>
+struct Red<float> {
+  using T = float;
+  static __device__ __forceinline__ T make(float x) { return fabsf(x); }
+  static __device__ __forceinline__ T mx(T a, T b) { return fmaxf(a, b); }
+  static __device__ __forceinline__ double value(T v) { return (double)v; }
+};
+
+// Per-cell contributions to (s_max, M_0..M_{NC-1}) (Eqs. 30, 36).
+template <int D, class M>
+__device__ __forceinline__ void cell_maxima(const M (&u)[D], M cs, const M (&Qf)[D][D + 2], typename Red<M>::T (&v)[kNV]) {
+  using R = Red<M>;
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    v[0] = R::mx(v[0], R::make(fabs(u[a]) + cs));
+#pragma unroll
+    for (int k = 0; k < D + 2; ++k) v[1 + k] = R::mx(v[1 + k], R::make(Qf[a][k]));
+  }
+}
+
+template <class M, int NT>
+__device__ __forceinline__ void block_max_store(typename Red<M>::T (&v)[kNV], double* __restrict__ part_slot, int cta,
+                                                int ncta, int* nparts_slot) {
+  using R = Red<M>;
+  using T = typename R::T;
+  __shared__ T red_s[NT / 32][kNV];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int j = 0; j < NV; ++j) {
-    double x = v[j];
+  for (int j = 0; j < kNV; ++j) {
+    T x = v[j];
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, off));
+    for (int off = 16; off > 0; off >>= 1) x = R::mx(x, __shfl_xor_sync(0xffffffffu, x, off));
     if (lane == 0) red_s[warp][j] = x;
   }
   __syncthreads();
   if (threadIdx.x < kNV) {
-    double x = 0.0;
-    if ((int)threadIdx.x < NV)
+    T x = red_s[0][threadIdx.x];
 #pragma unroll 4
-      for (int w = 0; w < NT / 32; ++w) x = fmax(x, red_s[w][threadIdx.x]);
-    part_slot[(long long)cta * kNV + threadIdx.x] = x;
+    for (int w = 1; w < NT / 32; ++w) x = R::mx(x, red_s[w][threadIdx.x]);
+    part_slot[(long long)cta * kNV + threadIdx.x] = R::value(x);
   }
   if (cta == 0 && threadIdx.x == 0) *nparts_slot = ncta;
 }
@@ -215,7 +288,7 @@ __device__ __forceinline__ void fold_partials(const double* __restrict__ part_sl
   for (int j = 0; j < kNV; ++j) v[j] = 0.0;
   for (int c = threadIdx.x; c < nparts; c += NT)
 #pragma unroll
-    for (int j = 0; j < kNV; ++j) v[j] = fmax(v[j], part_slot[(long long)c * kNV + j]);
+    for (int j = 0; j < kNV; ++j) v[j] = fmax(v[j], __ldg(part_slot + (long long)c * kNV + j));
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int j = 0; j < kNV; ++j) {
@@ -235,40 +308,40 @@ __device__ __forceinline__ void fold_partials(const double* __restrict__ part_sl
 }
 
 // ------------------------------------------------------------------------------------------
-// k_reduce: s_max and M_k of the current state (two-pass form; also the first step's maxima)
+// k_reduce: s_max and M_k of the current state (two-pass form; also feeds vlbm_get_beta)
 // ------------------------------------------------------------------------------------------
 template <int D, class S, int NT>
 __global__ void __launch_bounds__(NT) k_reduce(const S* __restrict__ fin, Scalars* __restrict__ sc, const KParams p,
                                                 const int pulled, double* __restrict__ part) {
   using M = typename Store<S>::M;
+  using R = Red<M>;
   constexpr int NC = D + 2;
   if (sc->done || sc->err) return;
   const int slot = (int)(sc->n & 1);
-  double v[NC + 1];
+  M wq[NC];
 #pragma unroll
-  for (int j = 0; j < NC + 1; ++j) v[j] = 0.0;
+  for (int k = 0; k < NC; ++k) wq[k] = StepScalars<M>::wq(sc, k);
+  typename R::T v[kNV];
+#pragma unroll
+  for (int j = 0; j < kNV; ++j) v[j] = typename R::T(0);
   bool bad = false;
   for (long long cell = (long long)blockIdx.x * NT + threadIdx.x; cell < p.plane; cell += (long long)gridDim.x * NT) {
     const int cx = (int)(cell % p.nx), cy = (int)(cell / p.nx);
     M fr[2 * D][NC], W[NC], u[D], Qf[D][NC], cs;
-    load_cell<D, S>(fin, p, cx, cy, pulled, fr, W, sc->wref);
-    bad |= !prim_flux<D, M>(p, W, u, Qf, cs);
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-      v[0] = fmax(v[0], (double)(fabs(u[a]) + cs));
-#pragma unroll
-      for (int k = 0; k < NC; ++k) v[1 + k] = fmax(v[1 + k], (double)fabs(Qf[a][k]));
-    }
+    load_cell<D, S>(fin, p, cx, cy, pulled, false, fr);
+    moments<D, M, Store<S>::kOffset>(fr, wq, W);
+    bad |= !prim_flux<D, M, true>(p, W, u, Qf, cs);
+    cell_maxima<D, M>(u, cs, Qf, v);
   }
   if (bad) atomicOr(&sc->err, ERR_NONPHYSICAL);
-  block_max_store<NC + 1, NT>(v, part + (long long)slot * p.max_parts * kNV, blockIdx.x, gridDim.x, &sc->nparts[slot]);
+  block_max_store<M, NT>(v, part + (long long)slot * p.max_parts * kNV, blockIdx.x, gridDim.x, &sc->nparts[slot]);
 }
 
 // ------------------------------------------------------------------------------------------
 // k_dt: link speed and time step of the next step (Eqs. 36-37), final-step shortening, and the
-// reciprocals the step kernels use.  One thread.
+// reciprocals the step kernels use.  One CTA folds the partial maxima; thread 0 decides.
 // ------------------------------------------------------------------------------------------
-constexpr int kNTD = 256;  // threads of the one-CTA scalar kernels
+constexpr int kNTD = 1024;  // threads of the one-CTA scalar kernels
 
 __global__ void __launch_bounds__(kNTD) k_dt(Scalars* sc, const KParams p, const double* __restrict__ part,
                                               double* hist_dt, double* hist_c, const double* sched) {
@@ -312,7 +385,12 @@ __global__ void __launch_bounds__(kNTD) k_dt(Scalars* sc, const KParams p, const
   sc->c_new = c;
   sc->inv_c = 1.0 / c;
   sc->dt = dt;
-  for (int k = 0; k < p.nc; ++k) sc->inv_M[k] = mx[1 + k] > 0.0 ? 1.0 / mx[1 + k] : 0.0;
+  sc->r_f = (float)sc->r;
+  sc->inv_c_f = (float)sc->inv_c;
+  for (int k = 0; k < p.nc; ++k) {
+    sc->inv_M[k] = mx[1 + k] > 0.0 ? 1.0 / mx[1 + k] : 0.0;
+    sc->inv_M_f[k] = (float)sc->inv_M[k];
+  }
   if (n < sc->hist_cap) {
     hist_dt[n] = dt;
     hist_c[n] = c;
@@ -330,27 +408,27 @@ __global__ void __launch_bounds__(kNTD) k_dt(Scalars* sc, const KParams p, const
 template <int D, class S, bool LOOK, int TX, int TY>
 struct TileGeom {
   static constexpr int NC = D + 2, Q = 2 * D;
-  static constexpr int H = LOOK ? 3 : 2;                   // W/u/Q region radius
+  static constexpr int H = LOOK ? 3 : 2;                          // u/Q region radius
   static constexpr int HY = D == 2 ? H : 0;
-  static constexpr int RX = TX + 2 * H, RY = TY + 2 * HY;  // region
+  static constexpr int RX = TX + 2 * H, RY = TY + 2 * HY;         // u/Q region
   static constexpr int SX = TX + 2 * (H - 1), SY = TY + 2 * (D == 2 ? H - 1 : 0);  // s, theta region
-  static constexpr int RB = LOOK ? 1 : 0;                  // relaxed ring
-  static constexpr int BX = TX + 2 * RB, BY = TY + 2 * (D == 2 ? RB : 0);
+  static constexpr int RB = LOOK ? 1 : 0, RBY = D == 2 ? RB : 0;  // relaxed ring
+  static constexpr int BX = TX + 2 * RB, BY = TY + 2 * RBY;       // relaxed region
   static constexpr int NT = TX * TY;
   using M = typename Store<S>::M;
-  static constexpr size_t smem_elems =
-      (size_t)D * RY * RX + (size_t)D * NC * RY * RX + (size_t)SY * SX * (D == 2 ? 2 : 1) + (LOOK ? (size_t)NC * BY * BX : 0);
+  static constexpr size_t smem_elems = (size_t)(D + D * NC) * RY * RX + (size_t)SY * SX * (D == 2 ? 2 : 1) +
+                                       (size_t)Q * NC * BY * BX;
   static constexpr size_t smem_bytes = smem_elems * sizeof(M);
 };
 
 // beta at region-local centre (sx, sy) of the s/theta arrays: box filter x then y (Sec. III D),
 // Sensor A (1D, Eq. 34) or Sensor B (2D, Eq. 35).
 template <int D, class M, int SX>
-__device__ __forceinline__ M sensor_beta(const KParams& p, const M* s_s, const M* s_t, int sx, int sy) {
-  if (p.beta_mode == 1) return (M)p.beta_const;
+__device__ __forceinline__ M sensor_beta(const KParams& p, const Coef<M>& c, const M* s_s, const M* s_t, int sx, int sy) {
+  if (p.beta_mode == 1) return c.beta_const;
   const M q = (M)0.25, h = (M)0.5;
   M sbar, tbar = (M)1;
-  if (D == 1) {
+  if constexpr (D == 1) {
     sbar = q * s_s[sx - 1] + h * s_s[sx] + q * s_s[sx + 1];
   } else {
     M rs[3], rt[3];
@@ -364,18 +442,17 @@ __device__ __forceinline__ M sensor_beta(const KParams& p, const M* s_s, const M
     sbar = q * rs[0] + h * rs[1] + q * rs[2];
     tbar = q * rt[0] + h * rt[1] + q * rt[2];
   }
-  M chi = (M)p.c_sensor * sbar * tbar;
+  M chi = c.c_sensor * sbar * tbar;
   chi = chi <= (M)0 ? (M)0 : (chi >= (M)1 ? (M)1 : chi);
-  return (M)p.beta_max - (M)(p.beta_max - p.beta_min) * chi;
+  return c.beta_max - c.dbeta * chi;
 }
 
 // Fused reprojection (c_old -> c_new, Eqs. 38-40) and relaxation (Eqs. 20, 22) of one cell:
-//   f*_{a,+-} = W/Q + s_a-term  +-  [ beta Q_a / c + (1 - 2 beta) r (f_{a+} - f_{a-}) / 2 ]
-//   with the D2Q4 K-term  +-(x/y)  (1 - 2 beta) r^2 ((f_x+ + f_x-) - (f_y+ + f_y-)) / 4,
+//   f*_{a,+-} = W/Q  +-  [ beta Q_a / c + (1 - 2 beta) r (f_{a+} - f_{a-}) / 2 ]
+//               (+ for x, - for y)  (1 - 2 beta) r^2 ((f_x+ + f_x-) - (f_y+ + f_y-)) / 4   (D2Q4 K-term),
 // r = c_old / c_new.  In FP32 storage the same update acts on the deviations (W/Q -> dW/Q).
 template <int D, class M>
-__device__ __forceinline__ void relax_cell(const M (&fr)[2 * D][D + 2], const M (&dW)[D + 2], const M (&Qc)[D][D + 2],
-                                           M beta, M r, M inv_c, M (&fo)[2 * D][D + 2]) {
+__device__ __forceinline__ void relax_cell(M (&f)[2 * D][D + 2], const M (&Qc)[D][D + 2], M beta, M r, M inv_c) {
   constexpr int NC = D + 2;
   const M om = (M)1 - (M)2 * beta;
   const M bq = beta * inv_c;
@@ -383,116 +460,99 @@ __device__ __forceinline__ void relax_cell(const M (&fr)[2 * D][D + 2], const M 
   const M omk = om * r * r * (M)0.25;
 #pragma unroll
   for (int k = 0; k < NC; ++k) {
-    const M w = dW[k] * (M)(1.0 / (2 * D));
-    const M gx = bq * Qc[0][k] + omr * (fr[1][k] - fr[0][k]);
+    const M sx = f[0][k] + f[1][k];
+    const M gx = bq * Qc[0][k] + omr * (f[1][k] - f[0][k]);
     if constexpr (D == 1) {
-      fo[0][k] = w - gx;
-      fo[1][k] = w + gx;
+      const M w = sx * (M)0.5;
+      f[0][k] = w - gx;
+      f[1][k] = w + gx;
     } else {
-      const M gy = bq * Qc[1][k] + omr * (fr[3][k] - fr[2][k]);
-      const M kk = omk * ((fr[0][k] + fr[1][k]) - (fr[2][k] + fr[3][k]));
-      fo[0][k] = w - gx + kk;
-      fo[1][k] = w + gx + kk;
-      fo[2][k] = w - gy - kk;
-      fo[3][k] = w + gy - kk;
+      const M sy = f[2][k] + f[3][k];
+      const M w = (sx + sy) * (M)0.25;
+      const M gy = bq * Qc[1][k] + omr * (f[3][k] - f[2][k]);
+      const M kk = omk * (sx - sy);
+      const M wx = w + kk, wy = w - kk;
+      f[0][k] = wx - gx;
+      f[1][k] = wx + gx;
+      f[2][k] = wy - gy;
+      f[3][k] = wy + gy;
     }
   }
 }
 
 template <int D, class S, bool LOOK, bool BETA_OUT, int TX, int TY>
 __global__ void __launch_bounds__(TX * TY) k_tile(const S* __restrict__ fin, S* __restrict__ fout, Scalars* __restrict__ sc,
-                                                    const KParams p, const int pulled, const double* __restrict__ invM_src,
+                                                    const KParams p, const int pulled,
+                                                    const typename Store<S>::M* __restrict__ invM_src,
                                                     double* __restrict__ beta_out, double* __restrict__ part) {
   using G = TileGeom<D, S, LOOK, TX, TY>;
   using M = typename G::M;
   constexpr int NC = G::NC, Q = G::Q, H = G::H, HY = G::HY, RX = G::RX, RY = G::RY, SX = G::SX, SY = G::SY;
-  constexpr int NT = G::NT;
+  constexpr int RB = G::RB, RBY = G::RBY, BX = G::BX, BY = G::BY, NT = G::NT;
+  constexpr bool OFF = Store<S>::kOffset;
   if (!BETA_OUT && !sc->active) return;
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   M* s_u = reinterpret_cast<M*>(smem_raw);  // [D][RY][RX]
   M* s_Q = s_u + D * RY * RX;               // [D][NC][RY][RX]
   M* s_s = s_Q + D * NC * RY * RX;          // [SY][SX]
-  M* s_t = s_s + SY * SX;                   // [SY][SX]      (2D)
-  M* s_x = s_t + (D == 2 ? SY * SX : 0);    // [NC][BY][BX]  (look-ahead exchange)
+  M* s_t = s_s + SY * SX;                   // [SY][SX]          (2D)
+  M* s_f = s_t + (D == 2 ? SY * SX : 0);    // [Q][NC][BY][BX]   populations of the relaxed region
 
+  const Coef<M>& co = coef<M>(p);
   const int x0 = blockIdx.x * TX, y0 = (D == 2) ? blockIdx.y * TY : 0;
-  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
-  const int gx = x0 + tx, gy = y0 + ty;
-  const bool own_in = gx < p.nx && gy < p.ny;
+  M wq[NC];
+#pragma unroll
+  for (int k = 0; k < NC; ++k) wq[k] = StepScalars<M>::wq(sc, k);
+  // Interior tile: every region position and its pull sources lie inside the domain, so no
+  // boundary rule is evaluated (uniform per CTA).
+  const bool interior = x0 - H - 1 >= 0 && x0 + TX + H + 1 <= p.nx &&
+                        (D == 1 || (y0 - HY - 1 >= 0 && y0 + TY + HY + 1 <= p.ny));
 
-  const M r = (M)sc->r, inv_c = (M)sc->inv_c;
-  M invM[NC];
-#pragma unroll
-  for (int k = 0; k < NC; ++k) invM[k] = (M)invM_src[k];
-  const double* wref = sc->wref;
-  bool bad = false;
-
-  // ---- phase A: primitives and flux on the region; the own cell keeps its populations ----
-  M fr[Q][NC], Wown[NC];
-  {
-    const int cx = nb_index(gx, p.nx, p.bc[0], p.bc[1]);
-    const int cy = (D == 2) ? nb_index(gy, p.ny, p.bc[2], p.bc[3]) : 0;
-    load_cell<D, S>(fin, p, cx, cy, pulled, fr, Wown, wref);
-    M u[D], Qf[D][NC], cs;
-    bad |= !prim_flux<D, M>(p, Wown, u, Qf, cs) && own_in;
-    const int ri = (ty + HY) * RX + (tx + H);
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-      s_u[a * RY * RX + ri] = u[a];
-#pragma unroll
-      for (int k = 0; k < NC; ++k) s_Q[(a * NC + k) * RY * RX + ri] = Qf[a][k];
-    }
-  }
-  constexpr int HALO = RX * RY - TX * TY;
-  for (int h = threadIdx.x; h < HALO; h += NT) {
-    int rx, ry;
-    if (h < HY * RX) {
-      ry = h / RX;
-      rx = h % RX;
-    } else if (h < HY * RX + TY * 2 * H) {
-      const int hh = h - HY * RX;
-      ry = HY + hh / (2 * H);
-      const int c = hh % (2 * H);
-      rx = c < H ? c : TX + c;
-    } else {
-      const int hh = h - HY * RX - TY * 2 * H;
-      ry = HY + TY + hh / RX;
-      rx = hh % RX;
-    }
+  // ---- phase A: populations, primitives and flux over the region (row-major, coalesced) ----
+  for (int idx = threadIdx.x; idx < RX * RY; idx += NT) {
+    const int rx = idx % RX, ry = idx / RX;
     const int px = x0 - H + rx, py = y0 - HY + ry;
-    const int cx = nb_index(px, p.nx, p.bc[0], p.bc[1]);
-    const int cy = (D == 2) ? nb_index(py, p.ny, p.bc[2], p.bc[3]) : 0;
-    M f2[Q][NC], W[NC], u[D], Qf[D][NC], cs;
-    load_cell<D, S>(fin, p, cx, cy, pulled, f2, W, wref);
-    bad |= !prim_flux<D, M>(p, W, u, Qf, cs);
-    const int ri = ry * RX + rx;
+    const int cx = interior ? px : nb_index(px, p.nx, p.bc[0], p.bc[1]);
+    const int cy = (D == 2) ? (interior ? py : nb_index(py, p.ny, p.bc[2], p.bc[3])) : 0;
+    M fr[Q][NC], W[NC], u[D], Qf[D][NC], cs;
+    load_cell<D, S>(fin, p, cx, cy, pulled, interior, fr);
+    moments<D, M, OFF>(fr, wq, W);
+    prim_flux<D, M, false>(p, W, u, Qf, cs);
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-      s_u[a * RY * RX + ri] = u[a];
+      s_u[a * RY * RX + idx] = u[a];
 #pragma unroll
-      for (int k = 0; k < NC; ++k) s_Q[(a * NC + k) * RY * RX + ri] = Qf[a][k];
+      for (int k = 0; k < NC; ++k) s_Q[(a * NC + k) * RY * RX + idx] = Qf[a][k];
+    }
+    const int bx = rx - (H - RB), by = ry - (HY - RBY);
+    if (!BETA_OUT && bx >= 0 && bx < BX && by >= 0 && by < BY) {
+#pragma unroll
+      for (int i = 0; i < Q; ++i)
+#pragma unroll
+        for (int k = 0; k < NC; ++k) s_f[(i * NC + k) * BY * BX + by * BX + bx] = fr[i][k];
     }
   }
-  if (bad) atomicOr(&sc->err, ERR_NONPHYSICAL);
   __syncthreads();
 
   // ---- phase B: activity s (Eqs. 28-31) and Ducros ratio theta (Eqs. 32-33) ----
   if (p.beta_mode == 0) {
-    const M inv2dx = (M)p.inv2dx, eps = (M)p.ducros_eps;
+    M invM[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) invM[k] = invM_src[k];
     for (int j = threadIdx.x; j < SX * SY; j += NT) {
       const int sx = j % SX, sy = j / SX;
       const int px = x0 - (H - 1) + sx;
       const int py = y0 - (D == 2 ? H - 1 : 0) + sy;
-      const int rx = centre_pos(px, p.nx, p.bc[0], p.bc[1]) - (x0 - H);
-      const int ry = (D == 2) ? centre_pos(py, p.ny, p.bc[2], p.bc[3]) - (y0 - HY) : 0;
+      const int rx = (interior ? px : centre_pos(px, p.nx, p.bc[0], p.bc[1])) - (x0 - H);
+      const int ry = (D == 2) ? (interior ? py : centre_pos(py, p.ny, p.bc[2], p.bc[3])) - (y0 - HY) : 0;
       const int c = ry * RX + rx;
       M acc = 0;
 #pragma unroll
       for (int k = 0; k < NC; ++k) {
         const M* qx = s_Q + (0 * NC + k) * RY * RX;
         M jk = qx[c + 1] - qx[c - 1];
-        if (D == 2) {
+        if constexpr (D == 2) {
           const M* qy = s_Q + ((D - 1) * NC + k) * RY * RX;
           jk += qy[c + RX] - qy[c - RX];
         }
@@ -500,145 +560,91 @@ __global__ void __launch_bounds__(TX * TY) k_tile(const S* __restrict__ fin, S* 
         acc += sh * sh;
       }
       s_s[j] = sqrt(acc * (M)(1.0 / NC));
-      if (D == 2) {
+      if constexpr (D == 2) {
         const M* ux = s_u;
         const M* uy = s_u + RY * RX;
-        const M dil = ((ux[c + 1] - ux[c - 1]) + (uy[c + RX] - uy[c - RX])) * inv2dx;
-        const M vort = ((uy[c + 1] - uy[c - 1]) - (ux[c + RX] - ux[c - RX])) * inv2dx;
-        s_t[j] = dil * dil / (dil * dil + vort * vort + eps);
+        const M dil = ((ux[c + 1] - ux[c - 1]) + (uy[c + RX] - uy[c - RX])) * co.inv2dx;
+        const M vort = ((uy[c + 1] - uy[c - 1]) - (ux[c + RX] - ux[c - RX])) * co.inv2dx;
+        s_t[j] = dil * dil / (dil * dil + vort * vort + co.eps);
       }
     }
     __syncthreads();
   }
 
-  // ---- phase C: beta of the own cell; BETA_OUT writes it and stops ----
-  const int ocx = centre_pos(gx, p.nx, p.bc[0], p.bc[1]) - (x0 - (H - 1));
-  const int ocy = (D == 2) ? centre_pos(gy, p.ny, p.bc[2], p.bc[3]) - (y0 - (H - 1)) : 0;
-  const M beta = sensor_beta<D, M, SX>(p, s_s, s_t, ocx, ocy);
-  if (BETA_OUT) {
-    if (own_in) beta_out[(long long)gy * p.nx + gx] = (double)beta;
-    return;
+  // ---- phase C/D: beta, fused reprojection + relaxation, single write ----
+  const M r = StepScalars<M>::r(sc), inv_c = StepScalars<M>::inv_c(sc);
+  for (int idx = threadIdx.x; idx < BX * BY; idx += NT) {
+    const int bx = idx % BX, by = idx / BX;
+    const int px = x0 - RB + bx, py = y0 - RBY + by;
+    const bool in_tile = bx >= RB && bx < RB + TX && by >= RBY && by < RBY + TY;
+    const bool in_dom = px >= 0 && px < p.nx && py >= 0 && py < p.ny;
+    // ring positions beyond a zero-gradient side are never read (their pulls land on the edge)
+    if (!in_tile && (centre_pos(px, p.nx, p.bc[0], p.bc[1]) != px ||
+                     (D == 2 && centre_pos(py, p.ny, p.bc[2], p.bc[3]) != py)))
+      continue;
+    const int ccx = centre_pos(px, p.nx, p.bc[0], p.bc[1]) - (x0 - (H - 1));
+    const int ccy = (D == 2) ? centre_pos(py, p.ny, p.bc[2], p.bc[3]) - (y0 - (H - 1)) : 0;
+    const M beta = sensor_beta<D, M, SX>(p, co, s_s, s_t, ccx, ccy);
+    if constexpr (BETA_OUT) {
+      if (in_dom) beta_out[(long long)py * p.nx + px] = (double)beta;
+      continue;
+    } else {
+      M f[Q][NC], Qc[D][NC];
+      const int ri = (by + (HY - RBY)) * RX + (bx + (H - RB));
+#pragma unroll
+      for (int i = 0; i < Q; ++i)
+#pragma unroll
+        for (int k = 0; k < NC; ++k) f[i][k] = s_f[(i * NC + k) * BY * BX + idx];
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int k = 0; k < NC; ++k) Qc[a][k] = s_Q[(a * NC + k) * RY * RX + ri];
+      relax_cell<D, M>(f, Qc, beta, r, inv_c);
+      if (in_tile && in_dom) {
+        const long long cell = (long long)py * p.nx + px;
+#pragma unroll
+        for (int i = 0; i < Q; ++i)
+#pragma unroll
+          for (int k = 0; k < NC; ++k) fout[(i * NC + k) * (int)p.plane + (int)cell] = (S)f[i][k];
+      }
+      if constexpr (LOOK) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i)
+#pragma unroll
+          for (int k = 0; k < NC; ++k) s_f[(i * NC + k) * BY * BX + idx] = f[i][k];
+      }
+    }
   }
 
-  // ---- phase D: fused reprojection + relaxation of the own cell, single write ----
-  M dWown[NC], Qown[D][NC];
-  {
-    const int ri = (ty + HY) * RX + (tx + H);
+  // ---- look-ahead: W^{n+1}(x) = sum_i f*_i(x - sigma_i) of the tile, reduced for the next step ----
+  if constexpr (LOOK && !BETA_OUT) {
+    __syncthreads();
+    using R = Red<M>;
+    typename R::T v[kNV];
 #pragma unroll
-    for (int k = 0; k < NC; ++k) {
-      dWown[k] = Wown[k];
-      if (Store<S>::kOffset) dWown[k] -= (M)(Q * wref[k]);
+    for (int j = 0; j < kNV; ++j) v[j] = typename R::T(0);
+    bool bad = false;
+    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    const int gx = x0 + tx, gy = y0 + ty;
+    if (gx < p.nx && gy < p.ny) {
+      M W[NC];
 #pragma unroll
-      for (int a = 0; a < D; ++a) Qown[a][k] = s_Q[(a * NC + k) * RY * RX + ri];
-    }
-  }
-  M fo[Q][NC];
-  if (Store<S>::kOffset) {
-    // deviation sums from the stored deviations directly (no W_ref round trip)
+      for (int k = 0; k < NC; ++k) W[k] = wq[k];
 #pragma unroll
-    for (int k = 0; k < NC; ++k) {
-      M acc = 0;
+      for (int i = 0; i < Q; ++i) {
+        const int qx = centre_pos(gx - sig_x(i), p.nx, p.bc[0], p.bc[1]) - (x0 - RB);
+        const int qy = (D == 2) ? centre_pos(gy - sig_y(i), p.ny, p.bc[2], p.bc[3]) - (y0 - RBY) : 0;
 #pragma unroll
-      for (int i = 0; i < Q; ++i) acc += fr[i][k];
-      dWown[k] = acc;
-    }
-  }
-  relax_cell<D, M>(fr, dWown, Qown, beta, r, inv_c, fo);
-  if (own_in) {
-    const long long cell = (long long)gy * p.nx + gx;
-#pragma unroll
-    for (int i = 0; i < Q; ++i)
-#pragma unroll
-      for (int k = 0; k < NC; ++k) fout[(long long)(i * NC + k) * p.plane + cell] = (S)fo[i][k];
-  }
-  if constexpr (LOOK) {
-  // ---- look-ahead: relax the one-cell ring, stream into W^{n+1} of the tile, reduce it ----
-  constexpr int BX = G::BX, BY = G::BY, RB = G::RB;
-  constexpr int RING = BX * BY - TX * TY;
-  // ring cell handled by this thread (at most one: RING <= NT)
-  M fring[Q][NC];
-  int rbx = -1, rby = -1;
-  if ((int)threadIdx.x < RING) {
-    const int h = threadIdx.x;
-    if (D == 1) {
-      rby = 0;
-      rbx = h == 0 ? 0 : BX - 1;
-    } else if (h < BX) {
-      rby = 0;
-      rbx = h;
-    } else if (h < BX + 2 * TY) {
-      const int hh = h - BX;
-      rby = 1 + hh / 2;
-      rbx = (hh & 1) ? BX - 1 : 0;
-    } else {
-      rby = BY - 1;
-      rbx = h - BX - 2 * TY;
-    }
-    const int px = x0 - RB + rbx, py = y0 - (D == 2 ? RB : 0) + rby;
-    const bool needed = centre_pos(px, p.nx, p.bc[0], p.bc[1]) == px &&
-                        (D == 1 || centre_pos(py, p.ny, p.bc[2], p.bc[3]) == py);
-    if (needed) {
-      const int cx = nb_index(px, p.nx, p.bc[0], p.bc[1]);
-      const int cy = (D == 2) ? nb_index(py, p.ny, p.bc[2], p.bc[3]) : 0;
-      M f2[Q][NC], W[NC];
-      load_cell<D, S>(fin, p, cx, cy, pulled, f2, W, wref);
-      const int ri = (py - (y0 - HY)) * RX + (px - (x0 - H));
-      M dW[NC], Qc[D][NC];
-#pragma unroll
-      for (int k = 0; k < NC; ++k) {
-        M acc = 0;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) acc += f2[i][k];
-        dW[k] = Store<S>::kOffset ? acc : W[k];
-#pragma unroll
-        for (int a = 0; a < D; ++a) Qc[a][k] = s_Q[(a * NC + k) * RY * RX + ri];
+        for (int k = 0; k < NC; ++k) W[k] += s_f[(i * NC + k) * BY * BX + qy * BX + qx];
       }
-      const int bsx = px - (x0 - (H - 1)), bsy = (D == 2) ? py - (y0 - (H - 1)) : 0;
-      const M b2 = sensor_beta<D, M, SX>(p, s_s, s_t, bsx, bsy);
-      relax_cell<D, M>(f2, dW, Qc, b2, r, inv_c, fring);
-    } else {
-      rbx = -1;
+      M u[D], Qf[D][NC], cs;
+      bad = !prim_flux<D, M, true>(p, W, u, Qf, cs);
+      cell_maxima<D, M>(u, cs, Qf, v);
     }
-  }
-  // exchange one direction at a time: W^{n+1}(x) = sum_i f*_i(x - sigma_i), i in lattice order
-  M Wn[NC];
-#pragma unroll
-  for (int k = 0; k < NC; ++k) Wn[k] = 0;
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < NC; ++k) {
-      s_x[(k * BY + (ty + (D == 2 ? RB : 0))) * BX + tx + RB] = fo[i][k];
-      if (rbx >= 0) s_x[(k * BY + rby) * BX + rbx] = fring[i][k];
-    }
-    __syncthreads();
-    if (own_in) {
-      const int qx = centre_pos(gx - sig_x(i), p.nx, p.bc[0], p.bc[1]) - (x0 - RB);
-      const int qy = (D == 2) ? centre_pos(gy - sig_y(i), p.ny, p.bc[2], p.bc[3]) - (y0 - RB) : 0;
-#pragma unroll
-      for (int k = 0; k < NC; ++k) Wn[k] += s_x[(k * BY + qy) * BX + qx];
-    }
-  }
-  double v[NC + 1];
-#pragma unroll
-  for (int j = 0; j < NC + 1; ++j) v[j] = 0.0;
-  if (own_in) {
-    if (Store<S>::kOffset)
-#pragma unroll
-      for (int k = 0; k < NC; ++k) Wn[k] += (M)(Q * wref[k]);
-    M u[D], Qf[D][NC], cs;
-    if (!prim_flux<D, M>(p, Wn, u, Qf, cs)) atomicOr(&sc->err, ERR_NONPHYSICAL);
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-      v[0] = fmax(v[0], (double)(fabs(u[a]) + cs));
-#pragma unroll
-      for (int k = 0; k < NC; ++k) v[1 + k] = fmax(v[1 + k], (double)fabs(Qf[a][k]));
-    }
-  }
-  const int slot = (int)(sc->n & 1);
-  block_max_store<NC + 1, NT>(v, part + (long long)slot * p.max_parts * kNV, blockIdx.y * gridDim.x + blockIdx.x,
-                              gridDim.x * gridDim.y, &sc->nparts[slot]);
+    if (bad) atomicOr(&sc->err, ERR_NONPHYSICAL);
+    const int slot = (int)(sc->n & 1);
+    block_max_store<M, NT>(v, part + (long long)slot * p.max_parts * kNV, blockIdx.y * gridDim.x + blockIdx.x,
+                           gridDim.x * gridDim.y, &sc->nparts[slot]);
   }
 }
 
@@ -646,6 +652,7 @@ __global__ void __launch_bounds__(TX * TY) k_tile(const S* __restrict__ fin, S* 
 // initialisation, readback
 // ------------------------------------------------------------------------------------------
 __global__ void k_init_begin(Scalars* sc) {
+  for (int k = 0; k < 4; ++k) sc->wq_f[k] = 0.0f;
   sc->n = 0;
   sc->t = 0.0;
   sc->active = 0;
@@ -660,18 +667,20 @@ template <int D, int NT>
 __global__ void __launch_bounds__(NT) k_reduce_W0(const double* __restrict__ W0, Scalars* __restrict__ sc, const KParams p,
                                                    double* __restrict__ part) {
   constexpr int NC = D + 2;
-  double v[1] = {0.0};
+  using R = Red<double>;
+  R::T v[kNV];
+#pragma unroll
+  for (int j = 0; j < kNV; ++j) v[j] = 0ull;
   bool bad = false;
   for (long long cell = (long long)blockIdx.x * NT + threadIdx.x; cell < p.plane; cell += (long long)gridDim.x * NT) {
     double W[NC], u[D], Qf[D][NC], cs;
 #pragma unroll
     for (int k = 0; k < NC; ++k) W[k] = W0[k * p.plane + cell];
-    bad |= !prim_flux<D, double>(p, W, u, Qf, cs);
-#pragma unroll
-    for (int a = 0; a < D; ++a) v[0] = fmax(v[0], fabs(u[a]) + cs);
+    bad |= !prim_flux<D, double, true>(p, W, u, Qf, cs);
+    cell_maxima<D, double>(u, cs, Qf, v);
   }
   if (bad) atomicOr(&sc->err, ERR_NONPHYSICAL);
-  block_max_store<1, NT>(v, part + (long long)1 * p.max_parts * kNV, blockIdx.x, gridDim.x, &sc->nparts[1]);
+  block_max_store<double, NT>(v, part + (long long)1 * p.max_parts * kNV, blockIdx.x, gridDim.x, &sc->nparts[1]);
 }
 
 // Per-block compensated (Neumaier) sums of W0_k (FP32-storage reference), fixed order.
@@ -714,6 +723,7 @@ __global__ void k_sum_final(const double* __restrict__ partial, int nblk, const 
       S = t;
     }
     sc->wref[k] = (S + Cc) / (double)p.plane / (double)p.q;
+    sc->wq_f[k] = (float)(p.q * sc->wref[k]);
   }
 }
 
@@ -736,21 +746,24 @@ template <int D, class S, int NT>
 __global__ void __launch_bounds__(NT) k_init_eq(const double* __restrict__ W0, S* __restrict__ fout, Scalars* __restrict__ sc,
                                                  const KParams p, double* __restrict__ part) {
   using M = typename Store<S>::M;
+  using R = Red<M>;
   constexpr int NC = D + 2, Q = 2 * D;
-  double v[NC + 1];
+  typename R::T v[kNV];
 #pragma unroll
-  for (int j = 0; j < NC + 1; ++j) v[j] = 0.0;
+  for (int j = 0; j < kNV; ++j) v[j] = typename R::T(0);
+  M wq[NC];
+#pragma unroll
+  for (int k = 0; k < NC; ++k) wq[k] = Store<S>::kOffset ? (M)(Q * sc->wref[k]) : (M)0;
   bool bad = false;
   const double c0 = sc->c_prev;
   for (long long cell = (long long)blockIdx.x * NT + threadIdx.x; cell < p.plane; cell += (long long)gridDim.x * NT) {
     double W[NC], u[D], Qf[D][NC], cs;
 #pragma unroll
     for (int k = 0; k < NC; ++k) W[k] = W0[k * p.plane + cell];
-    prim_flux<D, double>(p, W, u, Qf, cs);
-    M Ws[NC];
+    prim_flux<D, double, false>(p, W, u, Qf, cs);
+    M fr[Q][NC];
 #pragma unroll
-    for (int k = 0; k < NC; ++k) {
-      M acc = 0;
+    for (int k = 0; k < NC; ++k)
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
         const int a = i >> 1;
@@ -758,22 +771,15 @@ __global__ void __launch_bounds__(NT) k_init_eq(const double* __restrict__ W0, S
         const double fe = W[k] / (2.0 * D) + sgn * Qf[a][k] / (2.0 * c0);  // c_i.Q/(2c^2), |c_i| = c
         const S st = Store<S>::kOffset ? (S)(fe - sc->wref[k]) : (S)fe;
         fout[(long long)(i * NC + k) * p.plane + cell] = st;
-        acc += (M)st;
+        fr[i][k] = (M)st;
       }
-      if (Store<S>::kOffset) acc += (M)(Q * sc->wref[k]);
-      Ws[k] = acc;
-    }
-    M us[D], Qs[D][NC], css;
-    bad |= !prim_flux<D, M>(p, Ws, us, Qs, css);
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-      v[0] = fmax(v[0], (double)(fabs(us[a]) + css));
-#pragma unroll
-      for (int k = 0; k < NC; ++k) v[1 + k] = fmax(v[1 + k], (double)fabs(Qs[a][k]));
-    }
+    M Ws[NC], us[D], Qs[D][NC], css;
+    moments<D, M, Store<S>::kOffset>(fr, wq, Ws);
+    bad |= !prim_flux<D, M, true>(p, Ws, us, Qs, css);
+    cell_maxima<D, M>(us, css, Qs, v);
   }
   if (bad) atomicOr(&sc->err, ERR_NONPHYSICAL);
-  block_max_store<NC + 1, NT>(v, part, blockIdx.x, gridDim.x, &sc->nparts[0]);
+  block_max_store<M, NT>(v, part, blockIdx.x, gridDim.x, &sc->nparts[0]);
 }
 
 // W = sum_i f_i (FP32 storage: FP64 sum of the reference share and the deviations).
@@ -836,7 +842,10 @@ __global__ void __launch_bounds__(kNTD) k_beta_prep(Scalars* sc, const KParams p
   double mx[kNV];
   fold_partials<kNTD>(part + (long long)slot * p.max_parts * kNV, sc->nparts[slot], mx);
   if (threadIdx.x == 0)
-    for (int k = 0; k < p.nc; ++k) invM_beta[k] = mx[1 + k] > 0.0 ? 1.0 / mx[1 + k] : 0.0;
+    for (int k = 0; k < p.nc; ++k) {
+      invM_beta[k] = mx[1 + k] > 0.0 ? 1.0 / mx[1 + k] : 0.0;
+      reinterpret_cast<float*>(invM_beta + 4)[k] = (float)invM_beta[k];
+    }
 }
 
 __global__ void k_begin(Scalars* sc, double t_end) {
@@ -863,13 +872,14 @@ struct TileCfg<1> {  // 1D tiles of 256 cells
 };
 
 template <int D, class S, bool LOOK, bool BOUT>
-cudaError_t launch_tile_t(const Launch& L, const void* fin, void* fout, int pulled, const double* invM, double* beta_out) {
+cudaError_t launch_tile_t(const Launch& L, const void* fin, void* fout, int pulled, const void* invM, double* beta_out) {
   constexpr int TX = TileCfg<D>::TX, TY = TileCfg<D>::TY;
   using G = TileGeom<D, S, LOOK, TX, TY>;
   const KParams& p = *L.p;
   dim3 grid((p.nx + TX - 1) / TX, D == 2 ? (p.ny + TY - 1) / TY : 1);
   k_tile<D, S, LOOK, BOUT, TX, TY><<<grid, TX * TY, G::smem_bytes, L.stream>>>((const S*)fin, (S*)fout, L.sc, p, pulled,
-                                                                              invM, beta_out, L.part);
+                                                                              (const typename Store<S>::M*)invM, beta_out,
+                                                                              L.part);
   return cudaGetLastError();
 }
 
@@ -882,7 +892,7 @@ cudaError_t prepare_tile_t() {
 }
 
 template <class S, bool LOOK, bool BOUT>
-cudaError_t launch_tile_d(const Launch& L, const void* fin, void* fout, int pulled, const double* invM, double* beta_out) {
+cudaError_t launch_tile_d(const Launch& L, const void* fin, void* fout, int pulled, const void* invM, double* beta_out) {
   return L.p->dim == 1 ? launch_tile_t<1, S, LOOK, BOUT>(L, fin, fout, pulled, invM, beta_out)
                        : launch_tile_t<2, S, LOOK, BOUT>(L, fin, fout, pulled, invM, beta_out);
 }
@@ -943,10 +953,13 @@ cudaError_t launch_dt(const Launch& L) {
 }
 
 cudaError_t launch_step(const Launch& L, int precision, bool lookahead, const void* fin, void* fout, int pulled) {
-  const double* invM = reinterpret_cast<const double*>(reinterpret_cast<const char*>(L.sc) + offsetof(Scalars, inv_M));
-  if (precision == 0)
+  const char* base = reinterpret_cast<const char*>(L.sc);
+  if (precision == 0) {
+    const void* invM = base + offsetof(Scalars, inv_M);
     return lookahead ? launch_tile_d<double, true, false>(L, fin, fout, pulled, invM, nullptr)
                      : launch_tile_d<double, false, false>(L, fin, fout, pulled, invM, nullptr);
+  }
+  const void* invM = base + offsetof(Scalars, inv_M_f);
   return lookahead ? launch_tile_d<float, true, false>(L, fin, fout, pulled, invM, nullptr)
                    : launch_tile_d<float, false, false>(L, fin, fout, pulled, invM, nullptr);
 }
@@ -957,12 +970,12 @@ cudaError_t launch_beta(const Launch& L, int precision, const void* fin, int pul
   // slot writes for this state), then 1/M_k into the beta scratch
   cudaError_t e = launch_reduce(L, precision, fin, pulled);
   if (e != cudaSuccess) return e;
-  double* invM_beta = beta_out + p.plane;  // caller provides plane + 4 doubles
+  double* invM_beta = beta_out + p.plane;  // caller provides plane + 8 doubles (1/M_k in FP64, FP32)
   k_beta_prep<<<1, kNTD, 0, L.stream>>>(L.sc, p, L.part, invM_beta);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (precision == 0) return launch_tile_d<double, false, true>(L, fin, nullptr, pulled, invM_beta, beta_out);
-  return launch_tile_d<float, false, true>(L, fin, nullptr, pulled, invM_beta, beta_out);
+  return launch_tile_d<float, false, true>(L, fin, nullptr, pulled, invM_beta + 4, beta_out);
 }
 
 cudaError_t launch_init(const Launch& L, int precision, const double* W0, void* fout, double* partial, int nblk_sum) {

@@ -200,24 +200,30 @@ _BZT_STATES_FILE = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(
                                 "bzt_states_seed3.json")
 
 
-def bzt_states(seed: int = 3, accept: Optional[Callable[[float, float], bool]] = None):
-    """Left and right (rho, P) states of the BZT interface problem: the first two candidates of
-    the seed's stream accepted by `accept` (c_s^2 > 0 and fundamental derivative Gamma < 0).
-    Without a predicate, the states stored for seed 3 (written by the fixture script beside the
-    file, from the oracle's EOS) are returned."""
+def bzt_states(seed: int = 3, accept: Optional[Callable[[float, float], bool]] = None,
+               pair_ok: Optional[Callable[[tuple, tuple], bool]] = None):
+    """Left and right (rho, P) states of the BZT interface problem.  Candidates come from the
+    seed's stream; a candidate state is kept where `accept` holds (c_s^2 > 0 and fundamental
+    derivative Gamma < 0); consecutive kept states form (left, right) pairs, and the first pair for
+    which `pair_ok` holds (the flow it starts stays hyperbolic, Eq. 14) is returned.  Without
+    predicates, the pair stored for seed 3 (written by the fixture script beside the file, from the
+    oracle) is returned."""
     if accept is None:
         with open(_BZT_STATES_FILE) as fh:
             d = json.load(fh)
         if d["seed"] != seed:
             raise ValueError(f"stored BZT states are for seed {d['seed']}, not {seed}")
         return [tuple(d["left"]), tuple(d["right"])]
-    out = []
-    for rho, P in draw_bzt_candidates(seed, 10000):
-        if accept(rho, P):
-            out.append((rho, P))
-            if len(out) == 2:
-                return out
-    raise RuntimeError("no two accepted BZT states in 10000 draws")
+    kept = []
+    for rho, P in draw_bzt_candidates(seed, 20000):
+        if not accept(rho, P):
+            continue
+        kept.append((rho, P))
+        if len(kept) == 2:
+            if pair_ok is None or pair_ok(kept[0], kept[1]):
+                return kept
+            kept = []
+    raise RuntimeError("no accepted BZT state pair in 20000 draws")
 
 
 def bzt_interface_2d(p: Problem = BZT_2D, seed: int = 3, states=None, amp: float = 1e-3, modes: int = 16) -> np.ndarray:
