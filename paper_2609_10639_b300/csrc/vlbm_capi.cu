@@ -229,8 +229,8 @@ vlbm_status vlbm_create(const vlbm_grid* grid, const vlbm_eos* eos, const vlbm_p
   if (!grid || !eos || !params || !out) return VLBM_E_INVAL;
   if (grid->dim != 1 && grid->dim != 2) return VLBM_E_INVAL;
   const long long nx = grid->nx, ny = grid->dim == 1 ? 1 : grid->ny;
-  // 32-bit population offsets: 2D (D+2) nx ny values per buffer must stay below 2^31
-  const long long nvals = 2LL * grid->dim * (grid->dim + 2);
+  // 32-bit population offsets: 2D * 4 * nx * ny values per buffer must stay below 2^31
+  const long long nvals = 2LL * grid->dim * 4;
   if (nx < 1 || ny < 1 || nx > 2147483647LL || ny > 2147483647LL || nx * ny > 2147483647LL / nvals) return VLBM_E_INVAL;
   if (!(grid->x1 > grid->x0)) return VLBM_E_INVAL;
   for (int j = 0; j < 4; ++j)
@@ -318,7 +318,7 @@ vlbm_status vlbm_create(const vlbm_grid* grid, const vlbm_eos* eos, const vlbm_p
                  (params->algorithm == VLBM_ALGO_AUTO && params->precision == VLBM_FP32_STORE);
 
   vlbm_status st = VLBM_OK;
-  const size_t fbytes = (size_t)p.q * p.nc * p.plane * h->elem;
+  const size_t fbytes = (size_t)p.q * 4 * p.plane * h->elem;  // layout [i][y][x][4]
   h->scratch_elems = (size_t)p.nc * p.plane + p.plane + 8;
   h->nblk_sum = vlbm::sum_blocks(p);
   if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||

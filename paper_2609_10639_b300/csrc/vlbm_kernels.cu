@@ -1,7 +1,8 @@
 // CUDA kernels of the VLBM step (sm_103a).
 //
-// Populations live in HBM as structure-of-arrays planes [i][k][y][x] (lattice direction i in
-// {x-, x+, y-, y+}, conserved component k), double-buffered.  A buffer holds post-collision
+// Populations live in HBM as one plane per lattice direction i in {x-, x+, y-, y+}, each cell
+// holding its (D+2) conserved components contiguously in a 4-wide vector: [i][y][x][4] (one 128-bit
+// access per direction and cell in FP32 storage, two in FP64), double-buffered.  A buffer holds post-collision
 // populations; a step pulls them across the lattice links on read (exact transport, Eq. 21), so
 // each population is read once and written once per step.  The first step after vlbm_init reads
 // the equilibrium populations in place ("unpulled").
@@ -67,6 +68,43 @@ __device__ __forceinline__ int centre_pos(int j, int n, int lo, int hi) {
 __device__ __forceinline__ int sig_x(int i) { return i == 0 ? -1 : (i == 1 ? 1 : 0); }
 __device__ __forceinline__ int sig_y(int i) { return i == 2 ? -1 : (i == 3 ? 1 : 0); }
 
+// 4-wide vector access (one lattice direction of one cell: its components k = 0..3, slot 3 unused
+// in 1D).  FP32: one 128-bit access; FP64: two.
+__device__ __forceinline__ void ld4g(const float* p, float (&v)[4]) {
+  const float4 t = __ldg(reinterpret_cast<const float4*>(p));
+  v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
+}
+__device__ __forceinline__ void ld4g(const double* p, double (&v)[4]) {
+  const double2 a = __ldg(reinterpret_cast<const double2*>(p)), b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+  v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
+}
+__device__ __forceinline__ void st4g(float* p, const float (&v)[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st4g(double* p, const double (&v)[4]) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+}
+__device__ __forceinline__ void ld4s(const float* p, float (&v)[4]) {
+  const float4 t = *reinterpret_cast<const float4*>(p);
+  v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
+}
+__device__ __forceinline__ void ld4s(const double* p, double (&v)[4]) {
+  const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+  v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
+}
+__device__ __forceinline__ void st4s(float* p, const float (&v)[4]) { st4g(p, v); }
+__device__ __forceinline__ void st4s(double* p, const double (&v)[4]) { st4g(p, v); }
+
+// Reciprocal, quotient and square root: correctly rounded in FP64; in the FP32-storage path the
+// hardware approximations (<= 2 ulp), well inside that path's error budget.
+__device__ __forceinline__ double rcp_(double x) { return 1.0 / x; }
+__device__ __forceinline__ float rcp_(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double div_(double a, double b) { return a / b; }
+__device__ __forceinline__ float div_(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+__device__ __forceinline__ float sqrt_(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
+
 template <class M>
 __device__ __forceinline__ const Coef<M>& coef(const KParams& p);
 template <>
@@ -102,7 +140,7 @@ __device__ __forceinline__ void eos_eval(const KParams& p, const Coef<E>& c, E r
     cs2 = c.ggm1 * e;
   } else {  // polytropic van der Waals, Eqs. (16)-(17); c_s^2 by Eq. (13)
     const E T = (e + c.a * rho) * c.inv_cv;
-    const E inv_omb = (E)1 / ((E)1 - c.b * rho);
+    const E inv_omb = rcp_((E)1 - c.b * rho);
     const E RT_omb = c.R * T * inv_omb;
     P = rho * RT_omb - c.a * rho * rho;
     const E dPdT = c.R * rho * inv_omb;                                       // (dP/dT)_rho
@@ -135,7 +173,7 @@ __device__ __forceinline__ bool prim_flux(const KParams& p, const M (&W)[D + 2],
     P = (M)Pd;
     cs2 = (M)cd;
   } else {
-    const M inv_rho = (M)1 / rho;
+    const M inv_rho = rcp_(rho);
     M usq = 0;
 #pragma unroll
     for (int a = 0; a < D; ++a) {
@@ -148,7 +186,7 @@ __device__ __forceinline__ bool prim_flux(const KParams& p, const M (&W)[D + 2],
   bool ok = true;
   if (NEED_CS) {
     ok = (rho > (M)0) && (cs2 > (M)0) && isfinite(cs2) && isfinite(P);
-    cs = sqrt(cs2 > (M)0 ? cs2 : (M)0);
+    cs = sqrt_(cs2 > (M)0 ? cs2 : (M)0);
   }
 #pragma unroll
   for (int a = 0; a < D; ++a) {
@@ -177,15 +215,15 @@ struct Store<float> {
 };
 
 // Loads the populations of cell (cx, cy), pulled across the links (or in place), into fr[i][k].
-// `interior`: the caller guarantees that (cx, cy) and its four neighbours lie inside the domain
-// (no boundary rule needed).  Offsets are 32-bit (vlbm_create bounds Q (D+2) nx ny below 2^31).
+// Layout [i][y][x][4]: one vector access per direction.  `interior`: the caller guarantees that
+// (cx, cy) and its four neighbours lie inside the domain (no boundary rule needed).  Offsets are
+// 32-bit (vlbm_create bounds 2D * 4 * nx * ny below 2^31).
 template <int D, class S>
 __device__ __forceinline__ void load_cell(const S* __restrict__ fin, const KParams& p, int cx, int cy, int pulled,
                                           bool interior, typename Store<S>::M (&fr)[2 * D][D + 2]) {
   using M = typename Store<S>::M;
   constexpr int NC = D + 2, Q = 2 * D;
   const int plane = (int)p.plane;
-  int src[Q];
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     int sx = cx, sy = cy;
@@ -198,12 +236,24 @@ __device__ __forceinline__ void load_cell(const S* __restrict__ fin, const KPara
         if (D == 2) sy = nb_index(cy - sig_y(i), p.ny, p.bc[2], p.bc[3]);
       }
     }
-    src[i] = sy * p.nx + sx;
+    S v[4];
+    ld4g(fin + (i * plane + sy * p.nx + sx) * 4, v);
+#pragma unroll
+    for (int k = 0; k < NC; ++k) fr[i][k] = (M)v[k];
   }
+}
+
+// Stores one cell's populations f[i][k] (layout [i][y][x][4]).
+template <int D, class S, class M>
+__device__ __forceinline__ void store_cell(S* __restrict__ fout, const KParams& p, int cell, const M (&f)[2 * D][D + 2]) {
+  const int plane = (int)p.plane;
 #pragma unroll
-  for (int k = 0; k < NC; ++k)
+  for (int i = 0; i < 2 * D; ++i) {
+    S v[4];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) fr[i][k] = (M)__ldg(fin + ((i * NC + k) * plane + src[i]));
+    for (int k = 0; k < 4; ++k) v[k] = k < D + 2 ? (S)f[i][k] : (S)0;
+    st4g(fout + (i * plane + cell) * 4, v);
+  }
 }
 
 // Zeroth moment of one cell: W_k = sum_i f_i (direction pairs first); in FP32 storage the sum of
@@ -279,31 +329,46 @@ __device__ __forceinline__ void block_max_store(typename Red<M>::T (&v)[kNV], do
   if (cta == 0 && threadIdx.x == 0) *nparts_slot = ncta;
 }
 
-// Fold the partials of one slot with one CTA of NT threads: out[j] = max over CTAs (all threads).
+// Fold the partials of one slot with one CTA of NT threads into out[j] (valid in thread 0).  The
+// partials are non-negative doubles and are compared as 64-bit patterns on the integer pipe (a
+// single SM's FP64 pipe would make this fold cost tens of microseconds).
 template <int NT>
 __device__ __forceinline__ void fold_partials(const double* __restrict__ part_slot, int nparts, double (&out)[kNV]) {
-  __shared__ double red_s[NT / 32][kNV];
-  double v[kNV];
+  using T = unsigned long long;
+  __shared__ T red_s[NT / 32][kNV];
+  const T* bits = reinterpret_cast<const T*>(part_slot);
+  T v[kNV];
 #pragma unroll
-  for (int j = 0; j < kNV; ++j) v[j] = 0.0;
+  for (int j = 0; j < kNV; ++j) v[j] = 0ull;
   for (int c = threadIdx.x; c < nparts; c += NT)
 #pragma unroll
-    for (int j = 0; j < kNV; ++j) v[j] = fmax(v[j], __ldg(part_slot + (long long)c * kNV + j));
+    for (int j = 0; j < kNV; ++j) {
+      const T x = __ldg(bits + (long long)c * kNV + j);
+      v[j] = x > v[j] ? x : v[j];
+    }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int j = 0; j < kNV; ++j) {
-    double x = v[j];
+    T x = v[j];
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, off));
+    for (int off = 16; off > 0; off >>= 1) {
+      const T y = __shfl_xor_sync(0xffffffffu, x, off);
+      x = y > x ? y : x;
+    }
     if (lane == 0) red_s[warp][j] = x;
   }
   __syncthreads();
+  if (warp == 0) {
 #pragma unroll
-  for (int j = 0; j < kNV; ++j) {
-    double x = 0.0;
-#pragma unroll 4
-    for (int w = 0; w < NT / 32; ++w) x = fmax(x, red_s[w][j]);
-    out[j] = x;
+    for (int j = 0; j < kNV; ++j) {
+      T x = lane < NT / 32 ? red_s[lane][j] : 0ull;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const T y = __shfl_xor_sync(0xffffffffu, x, off);
+        x = y > x ? y : x;
+      }
+      out[j] = __longlong_as_double((long long)x);
+    }
   }
 }
 
@@ -416,8 +481,8 @@ struct TileGeom {
   static constexpr int BX = TX + 2 * RB, BY = TY + 2 * RBY;       // relaxed region
   static constexpr int NT = TX * TY;
   using M = typename Store<S>::M;
-  static constexpr size_t smem_elems = (size_t)(D + D * NC) * RY * RX + (size_t)SY * SX * (D == 2 ? 2 : 1) +
-                                       (size_t)Q * NC * BY * BX;
+  static constexpr size_t smem_elems = (size_t)D * 4 * RY * RX + (size_t)Q * 4 * BY * BX + (size_t)D * RY * RX +
+                                       (size_t)SY * SX * (D == 2 ? 2 : 1);
   static constexpr size_t smem_bytes = smem_elems * sizeof(M);
 };
 
@@ -493,11 +558,11 @@ __global__ void __launch_bounds__(TX * TY) k_tile(const S* __restrict__ fin, S* 
   if (!BETA_OUT && !sc->active) return;
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  M* s_u = reinterpret_cast<M*>(smem_raw);  // [D][RY][RX]
-  M* s_Q = s_u + D * RY * RX;               // [D][NC][RY][RX]
-  M* s_s = s_Q + D * NC * RY * RX;          // [SY][SX]
-  M* s_t = s_s + SY * SX;                   // [SY][SX]          (2D)
-  M* s_f = s_t + (D == 2 ? SY * SX : 0);    // [Q][NC][BY][BX]   populations of the relaxed region
+  M* s_Q = reinterpret_cast<M*>(smem_raw);  // [D][RY][RX][4]  flux Q_alpha of the region
+  M* s_f = s_Q + D * RY * RX * 4;           // [Q][BY][BX][4]  populations of the relaxed region
+  M* s_u = s_f + Q * BY * BX * 4;           // [D][RY][RX]     velocity of the region
+  M* s_s = s_u + D * RY * RX;               // [SY][SX]        activity s
+  M* s_t = s_s + SY * SX;                   // [SY][SX]        Ducros ratio (2D)
 
   const Coef<M>& co = coef<M>(p);
   const int x0 = blockIdx.x * TX, y0 = (D == 2) ? blockIdx.y * TY : 0;
@@ -522,15 +587,20 @@ __global__ void __launch_bounds__(TX * TY) k_tile(const S* __restrict__ fin, S* 
 #pragma unroll
     for (int a = 0; a < D; ++a) {
       s_u[a * RY * RX + idx] = u[a];
+      M v[4];
 #pragma unroll
-      for (int k = 0; k < NC; ++k) s_Q[(a * NC + k) * RY * RX + idx] = Qf[a][k];
+      for (int k = 0; k < 4; ++k) v[k] = k < NC ? Qf[a][k] : (M)0;
+      st4s(s_Q + (a * RY * RX + idx) * 4, v);
     }
     const int bx = rx - (H - RB), by = ry - (HY - RBY);
     if (!BETA_OUT && bx >= 0 && bx < BX && by >= 0 && by < BY) {
 #pragma unroll
-      for (int i = 0; i < Q; ++i)
+      for (int i = 0; i < Q; ++i) {
+        M v[4];
 #pragma unroll
-        for (int k = 0; k < NC; ++k) s_f[(i * NC + k) * BY * BX + by * BX + bx] = fr[i][k];
+        for (int k = 0; k < 4; ++k) v[k] = k < NC ? fr[i][k] : (M)0;
+        st4s(s_f + (i * BY * BX + by * BX + bx) * 4, v);
+      }
     }
   }
   __syncthreads();
@@ -547,25 +617,28 @@ __global__ void __launch_bounds__(TX * TY) k_tile(const S* __restrict__ fin, S* 
       const int rx = (interior ? px : centre_pos(px, p.nx, p.bc[0], p.bc[1])) - (x0 - H);
       const int ry = (D == 2) ? (interior ? py : centre_pos(py, p.ny, p.bc[2], p.bc[3])) - (y0 - HY) : 0;
       const int c = ry * RX + rx;
+      M qxp[4], qxm[4], qyp[4], qym[4];
+      ld4s(s_Q + (c + 1) * 4, qxp);
+      ld4s(s_Q + (c - 1) * 4, qxm);
+      if constexpr (D == 2) {
+        ld4s(s_Q + (RY * RX + c + RX) * 4, qyp);
+        ld4s(s_Q + (RY * RX + c - RX) * 4, qym);
+      }
       M acc = 0;
 #pragma unroll
       for (int k = 0; k < NC; ++k) {
-        const M* qx = s_Q + (0 * NC + k) * RY * RX;
-        M jk = qx[c + 1] - qx[c - 1];
-        if constexpr (D == 2) {
-          const M* qy = s_Q + ((D - 1) * NC + k) * RY * RX;
-          jk += qy[c + RX] - qy[c - RX];
-        }
+        M jk = qxp[k] - qxm[k];
+        if constexpr (D == 2) jk += qyp[k] - qym[k];
         const M sh = (M)0.5 * jk * invM[k];
         acc += sh * sh;
       }
-      s_s[j] = sqrt(acc * (M)(1.0 / NC));
+      s_s[j] = sqrt_(acc * (M)(1.0 / NC));
       if constexpr (D == 2) {
         const M* ux = s_u;
         const M* uy = s_u + RY * RX;
         const M dil = ((ux[c + 1] - ux[c - 1]) + (uy[c + RX] - uy[c - RX])) * co.inv2dx;
         const M vort = ((uy[c + 1] - uy[c - 1]) - (ux[c + RX] - ux[c - RX])) * co.inv2dx;
-        s_t[j] = dil * dil / (dil * dil + vort * vort + co.eps);
+        s_t[j] = div_(dil * dil, dil * dil + vort * vort + co.eps);
       }
     }
     __syncthreads();
@@ -592,26 +665,29 @@ __global__ void __launch_bounds__(TX * TY) k_tile(const S* __restrict__ fin, S* 
       M f[Q][NC], Qc[D][NC];
       const int ri = (by + (HY - RBY)) * RX + (bx + (H - RB));
 #pragma unroll
-      for (int i = 0; i < Q; ++i)
+      for (int i = 0; i < Q; ++i) {
+        M v[4];
+        ld4s(s_f + (i * BY * BX + idx) * 4, v);
 #pragma unroll
-        for (int k = 0; k < NC; ++k) f[i][k] = s_f[(i * NC + k) * BY * BX + idx];
-#pragma unroll
-      for (int a = 0; a < D; ++a)
-#pragma unroll
-        for (int k = 0; k < NC; ++k) Qc[a][k] = s_Q[(a * NC + k) * RY * RX + ri];
-      relax_cell<D, M>(f, Qc, beta, r, inv_c);
-      if (in_tile && in_dom) {
-        const long long cell = (long long)py * p.nx + px;
-#pragma unroll
-        for (int i = 0; i < Q; ++i)
-#pragma unroll
-          for (int k = 0; k < NC; ++k) fout[(i * NC + k) * (int)p.plane + (int)cell] = (S)f[i][k];
+        for (int k = 0; k < NC; ++k) f[i][k] = v[k];
       }
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        M v[4];
+        ld4s(s_Q + (a * RY * RX + ri) * 4, v);
+#pragma unroll
+        for (int k = 0; k < NC; ++k) Qc[a][k] = v[k];
+      }
+      relax_cell<D, M>(f, Qc, beta, r, inv_c);
+      if (in_tile && in_dom) store_cell<D, S, M>(fout, p, py * p.nx + px, f);
       if constexpr (LOOK) {
 #pragma unroll
-        for (int i = 0; i < Q; ++i)
+        for (int i = 0; i < Q; ++i) {
+          M v[4];
 #pragma unroll
-          for (int k = 0; k < NC; ++k) s_f[(i * NC + k) * BY * BX + idx] = f[i][k];
+          for (int k = 0; k < 4; ++k) v[k] = k < NC ? f[i][k] : (M)0;
+          st4s(s_f + (i * BY * BX + idx) * 4, v);
+        }
       }
     }
   }
@@ -634,8 +710,10 @@ __global__ void __launch_bounds__(TX * TY) k_tile(const S* __restrict__ fin, S* 
       for (int i = 0; i < Q; ++i) {
         const int qx = centre_pos(gx - sig_x(i), p.nx, p.bc[0], p.bc[1]) - (x0 - RB);
         const int qy = (D == 2) ? centre_pos(gy - sig_y(i), p.ny, p.bc[2], p.bc[3]) - (y0 - RBY) : 0;
+        M v[4];
+        ld4s(s_f + (i * BY * BX + qy * BX + qx) * 4, v);
 #pragma unroll
-        for (int k = 0; k < NC; ++k) W[k] += s_f[(i * NC + k) * BY * BX + qy * BX + qx];
+        for (int k = 0; k < NC; ++k) W[k] += v[k];
       }
       M u[D], Qf[D][NC], cs;
       bad = !prim_flux<D, M, true>(p, W, u, Qf, cs);
@@ -770,9 +848,9 @@ __global__ void __launch_bounds__(NT) k_init_eq(const double* __restrict__ W0, S
         const double sgn = (i & 1) ? 1.0 : -1.0;
         const double fe = W[k] / (2.0 * D) + sgn * Qf[a][k] / (2.0 * c0);  // c_i.Q/(2c^2), |c_i| = c
         const S st = Store<S>::kOffset ? (S)(fe - sc->wref[k]) : (S)fe;
-        fout[(long long)(i * NC + k) * p.plane + cell] = st;
         fr[i][k] = (M)st;
       }
+    store_cell<D, S, M>(fout, p, (int)cell, fr);
     M Ws[NC], us[D], Qs[D][NC], css;
     moments<D, M, Store<S>::kOffset>(fr, wq, Ws);
     bad |= !prim_flux<D, M, true>(p, Ws, us, Qs, css);
@@ -790,7 +868,9 @@ __global__ void __launch_bounds__(NT) k_get_W(const S* __restrict__ fin, const S
   const long long cell = (long long)blockIdx.x * NT + threadIdx.x;
   if (cell >= p.plane) return;
   const int cx = (int)(cell % p.nx), cy = (int)(cell / p.nx);
-  int src[Q];
+  double acc[NC];
+#pragma unroll
+  for (int k = 0; k < NC; ++k) acc[k] = 0.0;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     int sx = cx, sy = cy;
@@ -798,20 +878,16 @@ __global__ void __launch_bounds__(NT) k_get_W(const S* __restrict__ fin, const S
       sx = nb_index(cx - sig_x(i), p.nx, p.bc[0], p.bc[1]);
       if (D == 2) sy = nb_index(cy - sig_y(i), p.ny, p.bc[2], p.bc[3]);
     }
-    src[i] = sy * p.nx + sx;
+    S v[4];
+    ld4g(fin + (i * (int)p.plane + sy * p.nx + sx) * 4, v);
+#pragma unroll
+    for (int k = 0; k < NC; ++k) acc[k] += Store<S>::kOffset ? ((double)v[k] + sc->wref[k]) : (double)v[k];
   }
 #pragma unroll
-  for (int k = 0; k < NC; ++k) {
-    double acc = 0.0;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const double v = (double)fin[(long long)(i * NC + k) * p.plane + src[i]];
-      acc += Store<S>::kOffset ? (v + sc->wref[k]) : v;
-    }
-    W[k * p.plane + cell] = acc;
-  }
+  for (int k = 0; k < NC; ++k) W[k * p.plane + cell] = acc[k];
 }
 
+// Populations in the interface layout [i][k][y][x] (FP32 storage: reference share added in FP64).
 template <int D, class S, int NT>
 __global__ void __launch_bounds__(NT) k_get_f(const S* __restrict__ fin, const Scalars* __restrict__ sc, const KParams p,
                                                const int pulled, double* __restrict__ f) {
@@ -826,12 +902,11 @@ __global__ void __launch_bounds__(NT) k_get_f(const S* __restrict__ fin, const S
       sx = nb_index(cx - sig_x(i), p.nx, p.bc[0], p.bc[1]);
       if (D == 2) sy = nb_index(cy - sig_y(i), p.ny, p.bc[2], p.bc[3]);
     }
-    const long long src = (long long)sy * p.nx + sx;
+    S v[4];
+    ld4g(fin + (i * (int)p.plane + sy * p.nx + sx) * 4, v);
 #pragma unroll
-    for (int k = 0; k < NC; ++k) {
-      const double v = (double)fin[(long long)(i * NC + k) * p.plane + src];
-      f[(long long)(i * NC + k) * p.plane + cell] = Store<S>::kOffset ? v + sc->wref[k] : v;
-    }
+    for (int k = 0; k < NC; ++k)
+      f[(long long)(i * NC + k) * p.plane + cell] = Store<S>::kOffset ? (double)v[k] + sc->wref[k] : (double)v[k];
   }
 }
 
@@ -1029,3 +1104,4 @@ cudaError_t launch_begin(const Launch& L, double t_end) {
 }
 
 }  // namespace vlbm
+

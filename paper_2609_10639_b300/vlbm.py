@@ -236,3 +236,4 @@ class Solver:
         n = C.c_int32()
         _check(_lib.vlbm_launches_per_step(self._h, C.byref(n)), "vlbm_launches_per_step")
         return n.value
+

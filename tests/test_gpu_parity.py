@@ -291,23 +291,27 @@ def test_fp32_store_shock_positions_within_one_cell():
     # two jumps of similar size).
     thr = 0.1 * (ro.max() - ro.min())
 
-    def jumps(line):
+    def jumps(line, t):
         d = np.abs(np.diff(line))
-        pk = (d > thr) & (d >= np.roll(d, 1)) & (d >= np.roll(d, -1))
+        pk = (d > t) & (d >= np.roll(d, 1)) & (d >= np.roll(d, -1))
         return np.flatnonzero(pk)
 
     total = matched = 0
+    missed = []
     for axis in (0, 1):
         for j in range(rg.shape[1 - axis]):
             lg = rg[:, j] if axis == 0 else rg[j, :]
             lo = ro[:, j] if axis == 0 else ro[j, :]
-            jg, jo = jumps(lg), jumps(lo)
-            for a, b in ((jo, jg), (jg, jo)):
+            # detection above thr, matching above thr/2 (hysteresis for jumps near the threshold)
+            for a, b in ((jumps(lo, thr), jumps(lg, 0.5 * thr)), (jumps(lg, thr), jumps(lo, 0.5 * thr))):
                 for x in a:
                     total += 1
-                    matched += bool(len(b)) and np.abs(b - x).min() <= 1
+                    ok = bool(len(b)) and np.abs(b - x).min() <= 1
+                    matched += ok
+                    if not ok:
+                        missed.append((axis, j, int(x)))
     assert total > 100
-    assert matched / total >= 0.999, (matched, total)
+    assert matched / total >= 0.999, (matched, total, missed[:10])
 
 
 def test_fp32_store_1d_sod():
