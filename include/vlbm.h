@@ -156,6 +156,37 @@ vlbm_status vlbm_get_profile(vlbm_t h, double* ms_total, int64_t* launches);
 /* Number of kernel launches one time step issues (for launch accounting). */
 vlbm_status vlbm_launches_per_step(vlbm_t h, int32_t* launches);
 
+/* beta(x) of caller-owned FP64 populations without any device allocation.
+ *
+ * The paper has no counterpart: this entry point serves callers that cannot call cudaMalloc,
+ * such as an application whose device memory all belongs to its own pool allocator, code that
+ * must not allocate while a CUDA graph is being captured, or a loop with a fixed memory budget.
+ * It computes what vlbm_get_beta returns for a handle holding the same state (Eqs. 28-35 with
+ * the maxima of Eq. 30), but keeps all scratch (a scalar block, 1/M_k and per-CTA partial maxima)
+ * in one file-scope static device array of about 330 KiB inside the library, which every GPU that
+ * loads the library holds until the process exits.
+ *
+ *   grid, eos, params: as for vlbm_create (only the sensor fields of params are used).
+ *   f:        device pointer, FP64 populations in the library's storage layout [i][y][x][4] (2D x 4 x
+ *             ny nx values; component k of direction i at ((i ny + y) nx + x) 4 + k, slot 3 unused
+ *             in 1D), caller-owned;
+ *             in_place != 0: f holds the state itself (e.g. from vlbm_get_populations);
+ *             in_place == 0: f holds post-collision populations to be pulled across the links.
+ *   beta:     device pointer, ny nx FP64 values, caller-owned output.
+ *   cuda_stream: stream for the work (NULL: legacy default stream); the call returns without
+ *             waiting, beta is valid once the stream reaches this point.
+ *
+ * Limits and behaviour: at most 2,097,152 cells (nx ny); larger grids return VLBM_E_INVAL.  The
+ * first call on a device looks up the array's device address (cudaGetSymbolAddress) and sets the
+ * kernels' shared-memory attribute; make that first call before any stream capture.  The call
+ * allocates nothing (no cudaMalloc, cudaFree or allocating library routine).  Every call on a
+ * device shares the one array and leaves its contents behind; the call clears the scalar block
+ * at its start, and every other entry it reads it writes first.  Calls that overlap on the GPU
+ * (different streams without ordering) race on the array: order them, e.g. one stream.  A
+ * non-physical state is not reported (use a handle for that); beta is then meaningless. */
+vlbm_status vlbm_beta_noalloc(const vlbm_grid* grid, const vlbm_eos* eos, const vlbm_params* params, const double* f,
+                              int32_t in_place, double* beta, void* cuda_stream);
+
 /* Human-readable name of a status code (static storage). */
 const char* vlbm_status_string(vlbm_status s);
 

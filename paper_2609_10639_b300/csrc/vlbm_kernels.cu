@@ -23,6 +23,7 @@
 //               streams those populations into W^{n+1} of its cells and reduces them for the next
 //               step, so a step moves each population through HBM exactly twice.
 // k_dt is a single-thread kernel that turns the maxima into c, dt, r and 1/M_k on the device.
+#include "vlbm.h"
 #include "vlbm_internal.cuh"
 
 #include <cfloat>
@@ -1104,4 +1105,144 @@ cudaError_t launch_begin(const Launch& L, double t_end) {
 }
 
 }  // namespace vlbm
+
+// ==========================================================================================
+// Allocation-free beta(x) of caller-owned populations.
+//
+// For callers that cannot call cudaMalloc: an application whose device memory belongs entirely
+// to its own pool allocator, code that must not allocate while a CUDA graph is being captured,
+// or a loop with a fixed memory budget.  The scratch of the beta computation (the device scalar
+// block, 1/M_k and the per-CTA partial maxima) lives in one file-scope static device array
+// instead of memory owned by a vlbm handle.  The kernels are the ones vlbm_get_beta runs; the
+// maxima kernel is launched with one CTA per 256 cells so that its partials fit the array.
+// ==========================================================================================
+namespace vlbm {
+namespace {
+constexpr int kNoallocCtaCells = 256;
+constexpr int kNoallocMaxCtas = 8192;
+constexpr long long kNoallocMaxCells = (long long)kNoallocCtaCells * kNoallocMaxCtas;  // 2,097,152
+constexpr int kNoallocScalarsBytes = 1024;                                             // >= sizeof(Scalars)
+constexpr int kNoallocInvMBytes = 256;                                                 // 4 FP64 + 4 FP32
+constexpr size_t kNoallocBytes =
+    kNoallocScalarsBytes + kNoallocInvMBytes + (size_t)kNoallocMaxCtas * kNV * sizeof(double);
+static_assert(sizeof(Scalars) <= kNoallocScalarsBytes, "scalar block does not fit its slot");
+
+// Shared by every call on a device; holds the last call's contents until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+constexpr int kNoallocMaxDevices = 64;
+unsigned char* g_noalloc_addr[kNoallocMaxDevices] = {nullptr};  // device address, per device ordinal
+}  // namespace
+
+}  // namespace vlbm
+
+extern "C" vlbm_status vlbm_beta_noalloc(const vlbm_grid* grid, const vlbm_eos* eos, const vlbm_params* params,
+                                         const double* f, int32_t in_place, double* beta, void* cuda_stream) {
+  using namespace vlbm;
+  if (!grid || !eos || !params || !f || !beta) return VLBM_E_INVAL;
+  if (grid->dim != 1 && grid->dim != 2) return VLBM_E_INVAL;
+  const long long nx = grid->nx, ny = grid->dim == 1 ? 1 : grid->ny;
+  if (nx < 1 || ny < 1) return VLBM_E_INVAL;
+  if (nx * ny > kNoallocMaxCells) return VLBM_E_INVAL;  // beyond the fixed scratch: rejected
+  for (int j = 0; j < 4; ++j)
+    if (grid->bc[j] != VLBM_BC_PERIODIC && grid->bc[j] != VLBM_BC_ZEROGRAD) return VLBM_E_INVAL;
+  if ((grid->bc[0] == VLBM_BC_PERIODIC) != (grid->bc[1] == VLBM_BC_PERIODIC)) return VLBM_E_INVAL;
+  if (grid->dim == 2 && (grid->bc[2] == VLBM_BC_PERIODIC) != (grid->bc[3] == VLBM_BC_PERIODIC)) return VLBM_E_INVAL;
+  if (!(grid->x1 > grid->x0)) return VLBM_E_INVAL;
+  if (eos->kind == VLBM_EOS_IDEAL ? !(eos->gamma > 1.0)
+                                  : (eos->kind != VLBM_EOS_VDW || !(eos->a >= 0.0 && eos->b >= 0.0 && eos->R > 0.0 && eos->cv > 0.0)))
+    return VLBM_E_INVAL;
+  if (params->beta_mode != VLBM_BETA_SENSOR && params->beta_mode != VLBM_BETA_CONST) return VLBM_E_INVAL;
+  if (params->beta_mode == VLBM_BETA_SENSOR &&
+      !(params->beta_min > 0.0 && params->beta_min <= params->beta_max && params->beta_max <= 1.0 &&
+        params->c_sensor >= 0.0 && params->ducros_eps > 0.0))
+    return VLBM_E_INVAL;
+  if (params->beta_mode == VLBM_BETA_CONST && !(params->beta_const > 0.0 && params->beta_const <= 1.0))
+    return VLBM_E_INVAL;
+
+  // Set-up, once per device, with that device current: the device address of the static array.
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoallocMaxDevices) return VLBM_E_CUDA;
+  if (!g_noalloc_addr[dev]) {
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return VLBM_E_CUDA;
+    if (cudaFuncSetAttribute(k_tile<1, double, false, true, TileCfg<1>::TX, TileCfg<1>::TY>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)TileGeom<1, double, false, TileCfg<1>::TX, TileCfg<1>::TY>::smem_bytes) != cudaSuccess ||
+        cudaFuncSetAttribute(k_tile<2, double, false, true, TileCfg<2>::TX, TileCfg<2>::TY>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)TileGeom<2, double, false, TileCfg<2>::TX, TileCfg<2>::TY>::smem_bytes) != cudaSuccess)
+      return VLBM_E_CUDA;
+    g_noalloc_addr[dev] = static_cast<unsigned char*>(ptr);
+  }
+  unsigned char* base = g_noalloc_addr[dev];
+  Scalars* sc = reinterpret_cast<Scalars*>(base);
+  double* invM = reinterpret_cast<double*>(base + kNoallocScalarsBytes);
+  double* part = reinterpret_cast<double*>(base + kNoallocScalarsBytes + kNoallocInvMBytes);
+
+  KParams p{};
+  p.dim = grid->dim;
+  p.nc = grid->dim + 2;
+  p.q = 2 * grid->dim;
+  p.nx = (int)nx;
+  p.ny = (int)ny;
+  p.plane = nx * ny;
+  for (int j = 0; j < 4; ++j) p.bc[j] = grid->bc[j];
+  if (grid->dim == 1) p.bc[2] = p.bc[3] = VLBM_BC_ZEROGRAD;
+  p.dx = (grid->x1 - grid->x0) / (double)nx;
+  p.inv2dx = 1.0 / (2.0 * p.dx);
+  p.eos_kind = eos->kind;
+  p.gamma = eos->kind == VLBM_EOS_IDEAL ? eos->gamma : 1.0 + eos->R / eos->cv;
+  p.a = eos->a;
+  p.b = eos->b;
+  p.R = eos->R;
+  p.cv = eos->cv;
+  p.inv_cv = eos->kind == VLBM_EOS_VDW ? 1.0 / eos->cv : 0.0;
+  p.cfl = 0.5;
+  p.beta_mode = params->beta_mode;
+  p.beta_const = params->beta_const;
+  p.beta_min = params->beta_min;
+  p.beta_max = params->beta_max;
+  p.c_sensor = params->c_sensor;
+  p.ducros_eps = params->ducros_eps;
+  p.retarget_every = 1;
+  const int ncta = (int)((p.plane + kNoallocCtaCells - 1) / kNoallocCtaCells);
+  p.max_parts = ncta;
+  Coef<double>& c = p.cd;
+  c.gamma = p.gamma;
+  c.gm1 = p.gamma - 1.0;
+  c.ggm1 = p.gamma * (p.gamma - 1.0);
+  c.a = p.a;
+  c.b = p.b;
+  c.R = p.R;
+  c.inv_cv = p.inv_cv;
+  c.a_inv_cv = p.a * p.inv_cv;
+  c.c_sensor = p.c_sensor;
+  c.beta_max = p.beta_max;
+  c.dbeta = p.beta_max - p.beta_min;
+  c.beta_const = p.beta_const;
+  c.inv2dx = p.inv2dx;
+  c.eps = p.ducros_eps;
+
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const int pulled = in_place ? 0 : 1;
+  // The scalar block must start at zero (no error bit, step 0); the partials and 1/M_k are
+  // fully written by this call before they are read.
+  if (cudaMemsetAsync(sc, 0, sizeof(Scalars), s) != cudaSuccess) return VLBM_E_CUDA;
+  if (p.dim == 1) k_reduce<1, double, kNoallocCtaCells><<<ncta, kNoallocCtaCells, 0, s>>>(f, sc, p, pulled, part);
+  else k_reduce<2, double, kNoallocCtaCells><<<ncta, kNoallocCtaCells, 0, s>>>(f, sc, p, pulled, part);
+  k_beta_prep<<<1, kNTD, 0, s>>>(sc, p, part, invM);
+  if (p.dim == 1) {
+    constexpr int TX = TileCfg<1>::TX, TY = TileCfg<1>::TY;
+    k_tile<1, double, false, true, TX, TY><<<dim3((p.nx + TX - 1) / TX, 1), TX * TY,
+                                             TileGeom<1, double, false, TX, TY>::smem_bytes, s>>>(f, nullptr, sc, p, pulled,
+                                                                                                 invM, beta, part);
+  } else {
+    constexpr int TX = TileCfg<2>::TX, TY = TileCfg<2>::TY;
+    k_tile<2, double, false, true, TX, TY><<<dim3((p.nx + TX - 1) / TX, (p.ny + TY - 1) / TY), TX * TY,
+                                             TileGeom<2, double, false, TX, TY>::smem_bytes, s>>>(f, nullptr, sc, p, pulled,
+                                                                                                 invM, beta, part);
+  }
+  return cudaGetLastError() == cudaSuccess ? VLBM_OK : VLBM_E_CUDA;
+}
 

@@ -237,3 +237,30 @@ class Solver:
         _check(_lib.vlbm_launches_per_step(self._h, C.byref(n)), "vlbm_launches_per_step")
         return n.value
 
+
+def _config_structs(cfg: Config):
+    """(_Grid, _Eos, _Params) of a Config, for the handle-free entry point."""
+    ny = 1 if cfg.dim == 1 else cfg.ny
+    g = _Grid(cfg.dim, cfg.nx, ny, *[float(v) for v in cfg.extent], (C.c_int32 * 4)(*[BC[b] for b in cfg.bc]))
+    e = cfg.eos
+    eo = _Eos(0, e["gamma"], 0.0, 0.0, 0.0, 0.0) if e["kind"] == "ideal" else _Eos(1, 0.0, e["a"], e["b"], e["R"], e["cv"])
+    p = _Params(cfg.cfl, 0 if cfg.beta_mode == "sensor" else 1, cfg.beta_const, cfg.beta_min, cfg.beta_max,
+                cfg.c_sensor, cfg.ducros_eps, cfg.retarget_every, PRECISION[cfg.precision], ALGORITHM[cfg.algorithm])
+    return g, eo, p
+
+
+_lib.vlbm_beta_noalloc.argtypes = [C.POINTER(_Grid), C.POINTER(_Eos), C.POINTER(_Params), C.c_void_p, C.c_int32,
+                                   C.c_void_p, C.c_void_p]
+_lib.vlbm_beta_noalloc.restype = C.c_int
+
+
+def beta_noalloc(cfg: Config, f, out, in_place: bool = True, stream=None) -> None:
+    """beta(x) of caller-owned FP64 populations `f` (CUDA tensor [2D][D+2][ny][nx]) into the
+    caller-owned CUDA tensor `out` ([ny][nx]) without any device allocation (for callers that
+    cannot allocate; see vlbm_beta_noalloc in include/vlbm.h).  Asynchronous on `stream`."""
+    import torch
+
+    g, eo, p = _config_structs(cfg)
+    s = stream if stream is not None else torch.cuda.current_stream()
+    _check(_lib.vlbm_beta_noalloc(C.byref(g), C.byref(eo), C.byref(p), C.c_void_p(_ptr(f)), 1 if in_place else 0,
+                                  C.c_void_p(_ptr(out)), C.c_void_p(s.cuda_stream)), "vlbm_beta_noalloc")
