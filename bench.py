@@ -38,6 +38,9 @@ BYTES_PER_CELL = {"fp64": 256, "fp32_store": 128}
 # Algorithmic FP64 floating-point operations per 2D cell update (ideal gas, shock sensor) of the
 # fused step, FMA counted as 2, divide and square root as 1 each (count in the design notes).
 FP64_FLOPS_PER_CELL = 214
+# Algorithmic bytes of one adjoint step including the recomputation of the forward state (FP64):
+# recompute 256 + read the forward state 128 + read lambda 128 + write lambda 128.
+ADJ_BYTES_PER_CELL = 640
 SMS, FP64_FMA_PER_CLK_PER_SM = 148, 2
 
 
@@ -216,6 +219,35 @@ def time_e2e(prob, W0_host, precision, S, K, world):
     return dt, nbytes
 
 
+def time_adjoint(n_steps, K, world):
+    """Reverse-pass time of vlbm_adjoint over the forward time of the same run, on the adjoint
+    workload (1024^2 periodic vortex with density perturbation, J = sum g rho(T))."""
+    import torch
+
+    from paper_2609_10639_b300 import vlbm, workloads as wl
+
+    prob = wl.VORTEX_ADJOINT_2D
+    W0 = torch.from_numpy(wl.vortex_density_2d(prob)).cuda()
+    dJ = torch.zeros_like(W0)
+    dJ[0] = torch.from_numpy(wl.objective_weight(prob)).cuda()
+    s = vlbm.Solver.for_problem(prob)
+    s.init(W0)
+    s.step(8)  # warm-up of the forward kernels
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.init(W0)
+    torch.cuda.synchronize()
+    e0.record()
+    s.step(n_steps)
+    e1.record()
+    torch.cuda.synchronize()
+    fwd_ms = max_over_ranks(e0.elapsed_time(e1), world)
+    s.adjoint(W0, min(n_steps, 2 * K), K, dJ)  # warm-up of the adjoint kernels
+    dW0, deos = s.adjoint(W0, n_steps, K, dJ)
+    rev_ms = max_over_ranks(s.adjoint_timing(), world)
+    s.close()
+    return {"fwd_ms": fwd_ms, "rev_ms": rev_ms, "cells": prob.ncells, "steps": n_steps, "K": K}
+
+
 def oracle_sample(min_seconds=10.0, n=1024, chunk=5, max_steps=None):
     """The oracle (as it stands) on a bounded sample of the workload: the same input generator at
     n x n cells, stepped in chunks until min_seconds of CPU work (or max_steps) have run."""
@@ -298,6 +330,7 @@ def run_ours(args):
     W0_host = torch.from_numpy(W0_np).pin_memory()
     dt_e2e, nbytes = time_e2e(prob, W0_host, "fp64", S, K, world)
     e2e64 = world * cells * S * K / dt_e2e / 1e6
+    adj = time_adjoint(args.adjoint_steps, 32, world) if args.adjoint_steps > 0 else None
 
     if rank != 0:
         return
@@ -334,6 +367,15 @@ def run_ours(args):
                                         "traffic": None if t32 is None else t32 * cells,
                                         "kernel": "k_tile<2,float,lookahead> (FP32-storage step)",
                                         "kernel_ms": r32["kernel_ms_avg"], "peak_source": pk["source"]}},
+            "adjoint": None if adj is None else {
+                "workload": "vortex_adjoint_2d_1024 (J = sum g rho(T), checkpoints every 32 steps)",
+                "value": world * adj["cells"] * adj["steps"] / (adj["rev_ms"] * 1e-3) / 1e6, "unit": UNIT,
+                "dtype": "f64", "steps": adj["steps"], "forward_ms": adj["fwd_ms"], "reverse_ms": adj["rev_ms"],
+                "adjoint_over_forward": adj["rev_ms"] / adj["fwd_ms"],
+                "roofline": {"bound": "hbm", "unit": "GB/s", "peak": pk["hbm_gbs"],
+                             "achieved": ADJ_BYTES_PER_CELL * adj["cells"] * adj["steps"] / (adj["rev_ms"] * 1e-3) / 1e9,
+                             "frac": ADJ_BYTES_PER_CELL * adj["cells"] * adj["steps"] / (adj["rev_ms"] * 1e-3) / 1e9 / pk["hbm_gbs"],
+                             "traffic": None, "note": "algorithmic 640 B/cell: recompute 256, state 128, lambda 128 + 128"}},
         },
         "cpu_baseline": cpu,
         "e2e": {"value": e2e64, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
@@ -350,6 +392,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--substeps", type=int, default=32)
+    ap.add_argument("--adjoint-steps", type=int, default=1000, help="steps of the adjoint measurement (0: skip)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--only", choices=list(BYTES_PER_CELL), help="time one path only (profiling, sweeps)")
     ap.add_argument("--grid", type=int, default=0, help="with --only: n x n copy of the workload")

@@ -82,7 +82,8 @@ typedef struct {
   double beta_min;        /* sensor floor, 0 < beta_min <= beta_max <= 1 (Eqs. 34-35)            */
   double beta_max;        /* sensor ceiling                                                     */
   double c_sensor;        /* sensitivity C_sensor >= 0 (Eqs. 34-35)                              */
-  double ducros_eps;      /* regulariser epsilon > 0 of the Ducros ratio (Eq. 33)                */
+  double ducros_eps;      /* regulariser epsilon > 0 of the Ducros ratio (Eq. 33), in the units of */
+                          /* |grad u|^2 (physical central differences); 1e-6 keeps theta smooth   */
   int32_t retarget_every; /* retarget the link speed every k >= 1 steps (Sec. III E)            */
   int32_t precision;      /* vlbm_precision: FP64 populations, or FP32 storage of deviations    */
   int32_t algorithm;      /* vlbm_algorithm: how the two global maxima of a step are obtained   */
@@ -152,6 +153,35 @@ vlbm_status vlbm_time_step_kernel(vlbm_t h, int32_t reps, double* ms_per_launch)
  * count, and resets both (synchronises).  Turning profiling on or off also resets them. */
 vlbm_status vlbm_set_profiling(vlbm_t h, int32_t on);
 vlbm_status vlbm_get_profile(vlbm_t h, double* ms_total, int64_t* launches);
+
+/* Gradient of an objective of the final state with respect to the initial field and the EOS
+ * parameters (reverse mode of the whole run).  FP32-storage handles keep the checkpoints and the
+ * recomputed states in FP32 storage and evaluate the adjoint in FP64 at those states.
+ *
+ * Runs vlbm_init(W0) and n_steps steps (adaptive link speed, or the replayed schedule), storing
+ * the populations every checkpoint_every steps and recording the link-speed sequence; then walks
+ * the run backwards segment by segment, recomputing each segment's states from its checkpoint
+ * with the recorded link speeds and applying the adjoint of every step: streaming (Eq. 21),
+ * relaxation and equilibrium (Eqs. 20, 22), the shock sensor with its global flux maxima
+ * (Eqs. 28-35), reprojection (Eqs. 38-40), and flux and EOS Jacobians (Eqs. 10-17), and finally
+ * the adjoint of the initial equilibrium.  The link speeds are held fixed (not differentiated);
+ * the derivative of each maximum M_k goes to its first maximal element in (alpha, y, x) order;
+ * d|x|/dx = 0 at 0, d sqrt = 0 at 0, and clip() has derivative 0 at and beyond its bounds.
+ *
+ *   W0:      (D+2) ny nx initial field (host or device).
+ *   dJ_dWT:  (D+2) ny nx values dJ/dW(T) of the objective at the final state (host or device).
+ *   dJ_dW0:  output, (D+2) ny nx values dJ/dW0 (host or device).
+ *   dJ_deos: host[5] output dJ/d(gamma, a, b, R, cv) (the ideal gas uses gamma, van der Waals
+ *            a, b, R, cv), or NULL.
+ * Afterwards the handle holds the final state of the run (as after vlbm_step).  Device memory:
+ * (ceil(n_steps / checkpoint_every) + min(checkpoint_every, n_steps) + 2) population states plus
+ * 43 FP64 fields per cell.  Synchronises. */
+vlbm_status vlbm_adjoint(vlbm_t h, const double* W0, int64_t n_steps, int32_t checkpoint_every, const double* dJ_dWT,
+                         double* dJ_dW0, double* dJ_deos);
+
+/* Device time (ms) of the reverse pass (segment recomputation and adjoint steps) of the last
+ * vlbm_adjoint call. */
+vlbm_status vlbm_adjoint_timing(vlbm_t h, double* reverse_ms);
 
 /* Number of kernel launches one time step issues (for launch accounting). */
 vlbm_status vlbm_launches_per_step(vlbm_t h, int32_t* launches);

@@ -85,7 +85,7 @@ def eos6(eos: dict) -> np.ndarray:
     return np.array([1.0, 1.0 + eos["R"] / eos["cv"], eos["a"], eos["b"], eos["R"], eos["cv"]])
 
 
-def prm8(cfl=0.5, beta_mode="sensor", beta_const=1.0, beta_min=0.75, beta_max=1.0, c_sensor=4.0, ducros_eps=1e-12,
+def prm8(cfl=0.5, beta_mode="sensor", beta_const=1.0, beta_min=0.75, beta_max=1.0, c_sensor=4.0, ducros_eps=1e-6,
          retarget_every=1) -> np.ndarray:
     return np.array([cfl, 0.0 if beta_mode == "sensor" else 1.0, beta_const, beta_min, beta_max, c_sensor, ducros_eps,
                      float(retarget_every)])

@@ -6,6 +6,7 @@
 // and time step, so the host synchronises only once at the end of the call (or once per chunk
 // when an end time is given and the number of steps is not known in advance).
 #include "vlbm.h"
+#include "vlbm_adjoint.cuh"
 #include "vlbm_internal.cuh"
 
 #include <cmath>
@@ -47,6 +48,26 @@ struct vlbm_s {
   static constexpr int kChunk = 32;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // adjoint workspace (allocated on first use, grown when needed)
+  struct Adj {
+    double* ckpt = nullptr;   // checkpoint states
+    size_t ckpt_states = 0;
+    double* seg = nullptr;    // recomputed states of one segment
+    size_t seg_states = 0;
+    double* lam[2] = {nullptr, nullptr};
+    double* F = nullptr;      // workspace fields
+    double* pv = nullptr;
+    long long* pi = nullptr;
+    double* part = nullptr;
+    double* sched = nullptr;  // [c0, c_0, ..., c_{N-1}]
+    size_t sched_cap = 0;
+    double* dJ = nullptr;     // device copy of dJ/dW(T)
+    double* dW0 = nullptr;    // device copy of W0 / result
+    vlbm::AdjScalars* as = nullptr;
+    vlbm::AdjScalars* as_host = nullptr;
+    Scalars* sc_backup = nullptr;
+    double fwd_ms = 0.0, rev_ms = 0.0;
+  } adj;
   bool profile = false;            // bracket step-kernel launches with events
   std::vector<cudaEvent_t> pev;    // event pool, used in pairs
   size_t pev_used = 0;
@@ -365,6 +386,20 @@ vlbm_status vlbm_destroy(vlbm_t h) {
   cudaFree(h->part);
   cudaFree(h->scratch);
   cudaFree(h->fscratch);
+  cudaFree(h->adj.ckpt);
+  cudaFree(h->adj.seg);
+  cudaFree(h->adj.lam[0]);
+  cudaFree(h->adj.lam[1]);
+  cudaFree(h->adj.F);
+  cudaFree(h->adj.pv);
+  cudaFree(h->adj.pi);
+  cudaFree(h->adj.part);
+  cudaFree(h->adj.sched);
+  cudaFree(h->adj.dJ);
+  cudaFree(h->adj.dW0);
+  cudaFree(h->adj.as);
+  cudaFree(h->adj.sc_backup);
+  if (h->adj.as_host) cudaFreeHost(h->adj.as_host);
   for (cudaEvent_t e : h->pev) cudaEventDestroy(e);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
@@ -564,6 +599,122 @@ vlbm_status vlbm_get_profile(vlbm_t h, double* ms_total, int64_t* launches) {
   if (ms_total) *ms_total = tot;
   if (launches) *launches = (int64_t)(h->pev_used / 2);
   h->pev_used = 0;
+  return VLBM_OK;
+}
+
+vlbm_status vlbm_adjoint(vlbm_t h, const double* W0, int64_t n_steps, int32_t checkpoint_every, const double* dJ_dWT,
+                         double* dJ_dW0, double* dJ_deos) {
+  if (!h || !W0 || !dJ_dWT || !dJ_dW0 || n_steps < 1 || checkpoint_every < 1) return VLBM_E_INVAL;
+  auto& A = h->adj;
+  const KParams& p = h->p;
+  // population states are kept in the handle's storage precision (FP64, or FP32 deviations);
+  // sizes below are in doubles (an FP32 state takes half of one FP64 state's doubles)
+  const size_t state_vals = (size_t)p.q * 4 * p.plane;
+  const size_t state = h->precision == VLBM_FP64 ? state_vals : (state_vals + 1) / 2;
+  const size_t lam_state = state_vals;
+  const size_t wsz = (size_t)p.nc * p.plane;
+  const long long N = n_steps, K = checkpoint_every;
+  const size_t nseg = (size_t)((N + K - 1) / K);
+  const size_t segn = (size_t)(K < N ? K : N);
+  // workspace (grown on demand)
+  auto grow = [](double** ptr, size_t* cap, size_t need) -> bool {
+    if (*cap >= need && *ptr) return true;
+    cudaFree(*ptr);
+    *ptr = nullptr;
+    *cap = 0;
+    if (cudaMalloc(ptr, need * sizeof(double)) != cudaSuccess) return false;
+    *cap = need;
+    return true;
+  };
+  if (!grow(&A.ckpt, &A.ckpt_states, nseg * state) || !grow(&A.seg, &A.seg_states, segn * state) ||
+      !grow(&A.sched, &A.sched_cap, (size_t)N + 1))
+    return VLBM_E_NOMEM;
+  if (!A.as) {
+    if (cudaMalloc(&A.lam[0], lam_state * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&A.lam[1], lam_state * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&A.F, (size_t)vlbm::adj_num_fields() * p.plane * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&A.pv, 592 * 4 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&A.pi, 592 * 4 * sizeof(long long)) != cudaSuccess ||
+        cudaMalloc(&A.part, (size_t)vlbm::adj_part_entries(p) * 8 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&A.dJ, wsz * sizeof(double)) != cudaSuccess || cudaMalloc(&A.dW0, wsz * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&A.sc_backup, sizeof(Scalars)) != cudaSuccess ||
+        cudaMallocHost(&A.as_host, sizeof(vlbm::AdjScalars)) != cudaSuccess ||
+        cudaMalloc(&A.as, sizeof(vlbm::AdjScalars)) != cudaSuccess)
+      return VLBM_E_NOMEM;
+  }
+  VLBM_TRY(cudaMemcpyAsync(A.dW0, W0, wsz * sizeof(double), cudaMemcpyDefault, h->stream));
+  VLBM_TRY(cudaMemcpyAsync(A.dJ, dJ_dWT, wsz * sizeof(double), cudaMemcpyDefault, h->stream));
+
+  // ---- forward pass: checkpoints every K steps, recorded link speeds ----
+  VLBM_TRY(cudaEventRecord(h->ev0, h->stream));
+  vlbm_status st = vlbm_init(h, A.dW0);
+  if (st != VLBM_OK) return st;
+  double c0 = 0.0;
+  st = vlbm_get_time(h, nullptr, nullptr, &c0);
+  if (st != VLBM_OK) return st;
+  VLBM_TRY(cudaMemcpyAsync(reinterpret_cast<char*>(A.as) + offsetof(vlbm::AdjScalars, wref),
+                           reinterpret_cast<const char*>(h->sc) + offsetof(Scalars, wref), 4 * sizeof(double),
+                           cudaMemcpyDeviceToDevice, h->stream));
+  for (size_t sgi = 0; sgi < nseg; ++sgi) {
+    const int cur = (int)(h->n_host & 1);
+    VLBM_TRY(cudaMemcpyAsync(A.ckpt + sgi * state, h->buf[cur], state * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    const long long steps = (long long)((N - (long long)sgi * K) < K ? (N - (long long)sgi * K) : K);
+    int64_t done = 0;
+    st = vlbm_step(h, steps, 0.0, &done);
+    if (st != VLBM_OK) return st;
+    if (done != steps) return VLBM_E_STATE;
+  }
+  VLBM_TRY(cudaMemcpyAsync(A.sched, &c0, sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  VLBM_TRY(cudaMemcpyAsync(A.sched + 1, h->hist_c, N * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  VLBM_TRY(cudaMemcpyAsync(A.sc_backup, h->sc, sizeof(Scalars), cudaMemcpyDeviceToDevice, h->stream));
+  VLBM_TRY(cudaEventRecord(h->ev1, h->stream));
+
+  // ---- reverse pass ----
+  vlbm::AdjLaunch L{&p, A.as, h->stream, A.sched, A.F, A.pv, A.pi, A.part};
+  vlbm::Launch FL = launch_of(h, h->stream);
+  FL.sched = A.sched;
+  int li = (int)(N & 1);  // lambda^N lives in lam[li]
+  VLBM_TRY(vlbm::adj_terminal(L, A.dJ, A.lam[li]));
+  for (long long sgi = (long long)nseg - 1; sgi >= 0; --sgi) {
+    const long long n0 = sgi * K, n1 = (n0 + K < N) ? n0 + K : N;
+    VLBM_TRY(cudaMemcpyAsync(A.seg, A.ckpt + (size_t)sgi * state, state * sizeof(double), cudaMemcpyDeviceToDevice,
+                             h->stream));
+    if (n1 - n0 > 1) {  // recompute the segment's states with the recorded link speeds (two-pass form)
+      VLBM_TRY(vlbm::adj_replay_scalars(h->stream, h->sc, n0, A.sched, N + 1));
+      for (long long j = 0; j + 1 < n1 - n0; ++j) {
+        const int pulled = (n0 + j >= 1) ? 1 : 0;
+        double* fin = A.seg + (size_t)j * state;
+        double* fout = A.seg + (size_t)(j + 1) * state;
+        VLBM_TRY(vlbm::launch_reduce(FL, h->precision, fin, pulled));
+        VLBM_TRY(vlbm::launch_dt(FL));
+        VLBM_TRY(vlbm::launch_step(FL, h->precision, false, fin, fout, pulled));
+      }
+    }
+    for (long long n = n1 - 1; n >= n0; --n) {
+      const int pulled = n >= 1 ? 1 : 0;
+      VLBM_TRY(vlbm::adj_step(L, h->precision, A.seg + (size_t)(n - n0) * state, pulled, A.lam[li], A.lam[li ^ 1], n));
+      li ^= 1;
+    }
+  }
+  VLBM_TRY(vlbm::adj_init(L, A.dW0, A.lam[li], c0, A.dW0));
+  VLBM_TRY(cudaMemcpyAsync(h->sc, A.sc_backup, sizeof(Scalars), cudaMemcpyDeviceToDevice, h->stream));
+  VLBM_TRY(cudaEventRecord(h->ev0, h->stream));
+  VLBM_TRY(cudaMemcpyAsync(dJ_dW0, A.dW0, wsz * sizeof(double), cudaMemcpyDefault, h->stream));
+  VLBM_TRY(cudaMemcpyAsync(A.as_host, A.as, sizeof(vlbm::AdjScalars), cudaMemcpyDeviceToHost, h->stream));
+  VLBM_TRY(cudaStreamSynchronize(h->stream));
+  float r_ms = 0.f;
+  // ev0 was re-recorded at the end of the reverse pass: reverse = [ev1, ev0]
+  VLBM_TRY(cudaEventElapsedTime(&r_ms, h->ev1, h->ev0));
+  A.rev_ms = r_ms;
+  if (dJ_deos)
+    for (int j = 0; j < 5; ++j) dJ_deos[j] = A.as_host->eos[j];
+  st = sync_scalars(h);
+  return st;
+}
+
+vlbm_status vlbm_adjoint_timing(vlbm_t h, double* reverse_ms) {
+  if (!h || !reverse_ms) return VLBM_E_INVAL;
+  *reverse_ms = h->adj.rev_ms;
   return VLBM_OK;
 }
 

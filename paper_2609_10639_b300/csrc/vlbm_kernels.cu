@@ -22,8 +22,10 @@
 //   look-ahead: k_dt -> k_tile, where k_tile also relaxes a one-cell ring around its tile,
 //               streams those populations into W^{n+1} of its cells and reduces them for the next
 //               step, so a step moves each population through HBM exactly twice.
-// k_dt is a single-thread kernel that turns the maxima into c, dt, r and 1/M_k on the device.
+// k_dt is a one-CTA kernel that folds the partial maxima and turns them into c, dt, r and 1/M_k
+// on the device.
 #include "vlbm.h"
+#include "vlbm_device.cuh"
 #include "vlbm_internal.cuh"
 
 #include <cfloat>
@@ -32,346 +34,6 @@
 #include <type_traits>
 
 namespace vlbm {
-
-// ------------------------------------------------------------------------------------------
-// index rules
-// ------------------------------------------------------------------------------------------
-// Cell index read at position j along an axis of n cells: wrap (periodic) or clamp to the edge
-// (zero-gradient).
-__device__ __forceinline__ int nb_index(int j, int n, int lo, int hi) {
-  if (j < 0) {
-    if (lo == 0) {
-      do { j += n; } while (j < 0);
-      return j;
-    }
-    return 0;
-  }
-  if (j >= n) {
-    if (hi == 0) {
-      do { j -= n; } while (j >= n);
-      return j;
-    }
-    return n - 1;
-  }
-  return j;
-}
-
-// Position at which a stencil quantity "at" position j is evaluated: the edge cell beyond a
-// zero-gradient side (the ghost replicates the edge cell), j itself otherwise (periodic sides are
-// unwrapped; the region holds the wrapped values there).
-__device__ __forceinline__ int centre_pos(int j, int n, int lo, int hi) {
-  if (j < 0 && lo == 1) return 0;
-  if (j >= n && hi == 1) return n - 1;
-  return j;
-}
-
-// Lattice unit vectors sigma_i in the order {x-, x+, y-, y+} (Eq. 18).
-__device__ __forceinline__ int sig_x(int i) { return i == 0 ? -1 : (i == 1 ? 1 : 0); }
-__device__ __forceinline__ int sig_y(int i) { return i == 2 ? -1 : (i == 3 ? 1 : 0); }
-
-// 4-wide vector access (one lattice direction of one cell: its components k = 0..3, slot 3 unused
-// in 1D).  FP32: one 128-bit access; FP64: two.
-__device__ __forceinline__ void ld4g(const float* p, float (&v)[4]) {
-  const float4 t = __ldg(reinterpret_cast<const float4*>(p));
-  v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
-}
-__device__ __forceinline__ void ld4g(const double* p, double (&v)[4]) {
-  const double2 a = __ldg(reinterpret_cast<const double2*>(p)), b = __ldg(reinterpret_cast<const double2*>(p) + 1);
-  v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
-}
-__device__ __forceinline__ void st4g(float* p, const float (&v)[4]) {
-  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
-}
-__device__ __forceinline__ void st4g(double* p, const double (&v)[4]) {
-  reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
-  reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
-}
-__device__ __forceinline__ void ld4s(const float* p, float (&v)[4]) {
-  const float4 t = *reinterpret_cast<const float4*>(p);
-  v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
-}
-__device__ __forceinline__ void ld4s(const double* p, double (&v)[4]) {
-  const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
-  v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
-}
-__device__ __forceinline__ void st4s(float* p, const float (&v)[4]) { st4g(p, v); }
-__device__ __forceinline__ void st4s(double* p, const double (&v)[4]) { st4g(p, v); }
-
-// Reciprocal, quotient and square root: correctly rounded in FP64; in the FP32-storage path the
-// hardware approximations (<= 2 ulp), well inside that path's error budget.
-__device__ __forceinline__ double rcp_(double x) { return 1.0 / x; }
-__device__ __forceinline__ float rcp_(float x) { return __fdividef(1.0f, x); }
-__device__ __forceinline__ double div_(double a, double b) { return a / b; }
-__device__ __forceinline__ float div_(float a, float b) { return __fdividef(a, b); }
-__device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
-__device__ __forceinline__ float sqrt_(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
-
-template <class M>
-__device__ __forceinline__ const Coef<M>& coef(const KParams& p);
-template <>
-__device__ __forceinline__ const Coef<double>& coef<double>(const KParams& p) { return p.cd; }
-template <>
-__device__ __forceinline__ const Coef<float>& coef<float>(const KParams& p) { return p.cf; }
-
-// Step scalars in the arithmetic type of a path (the FP32 copies are written by k_dt).
-template <class M>
-struct StepScalars;
-template <>
-struct StepScalars<double> {
-  static __device__ __forceinline__ double r(const Scalars* s) { return s->r; }
-  static __device__ __forceinline__ double inv_c(const Scalars* s) { return s->inv_c; }
-  static __device__ __forceinline__ const double* inv_M(const Scalars* s) { return s->inv_M; }
-  static __device__ __forceinline__ double wq(const Scalars* s, int k) { return 0.0; }
-};
-template <>
-struct StepScalars<float> {
-  static __device__ __forceinline__ float r(const Scalars* s) { return s->r_f; }
-  static __device__ __forceinline__ float inv_c(const Scalars* s) { return s->inv_c_f; }
-  static __device__ __forceinline__ const float* inv_M(const Scalars* s) { return s->inv_M_f; }
-  static __device__ __forceinline__ float wq(const Scalars* s, int k) { return s->wq_f[k]; }
-};
-
-// ------------------------------------------------------------------------------------------
-// thermodynamics (Sec. II C)
-// ------------------------------------------------------------------------------------------
-template <class E>
-__device__ __forceinline__ void eos_eval(const KParams& p, const Coef<E>& c, E rho, E inv_rho, E e, E& P, E& cs2) {
-  if (p.eos_kind == 0) {  // ideal gas, Eq. (15)
-    P = c.gm1 * rho * e;
-    cs2 = c.ggm1 * e;
-  } else {  // polytropic van der Waals, Eqs. (16)-(17); c_s^2 by Eq. (13)
-    const E T = (e + c.a * rho) * c.inv_cv;
-    const E inv_omb = rcp_((E)1 - c.b * rho);
-    const E RT_omb = c.R * T * inv_omb;
-    P = rho * RT_omb - c.a * rho * rho;
-    const E dPdT = c.R * rho * inv_omb;                                       // (dP/dT)_rho
-    const E P_rho = RT_omb * inv_omb - (E)2 * c.a * rho + dPdT * c.a_inv_cv;  // (dP/drho)_e
-    const E P_e = dPdT * c.inv_cv;                                            // (dP/de)_rho
-    cs2 = P_rho + P * inv_rho * inv_rho * P_e;
-  }
-}
-
-// Primitives and flux of one state (Eqs. 1-2, 10); with NEED_CS also c_s and the physical-state
-// check (returns false for rho <= 0, c_s^2 <= 0 or non-finite values).  In the FP32 path the van
-// der Waals energy-to-temperature inversion and pressure run in FP64.
-template <int D, class M, bool NEED_CS>
-__device__ __forceinline__ bool prim_flux(const KParams& p, const M (&W)[D + 2], M (&u)[D], M (&Qf)[D][D + 2], M& cs) {
-  constexpr int NC = D + 2;
-  const M rho = W[0];
-  M P, cs2;
-  if (std::is_same<M, float>::value && p.eos_kind != 0) {
-    const double rd = (double)rho, ird = 1.0 / rd;
-    double usq = 0.0;
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-      const double ua = (double)W[1 + a] * ird;
-      u[a] = (M)ua;
-      usq += ua * ua;
-    }
-    const double e = (double)W[NC - 1] * ird - 0.5 * usq;
-    double Pd, cd;
-    eos_eval<double>(p, p.cd, rd, ird, e, Pd, cd);
-    P = (M)Pd;
-    cs2 = (M)cd;
-  } else {
-    const M inv_rho = rcp_(rho);
-    M usq = 0;
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-      u[a] = W[1 + a] * inv_rho;
-      usq += u[a] * u[a];
-    }
-    const M e = W[NC - 1] * inv_rho - (M)0.5 * usq;
-    eos_eval<M>(p, coef<M>(p), rho, inv_rho, e, P, cs2);
-  }
-  bool ok = true;
-  if (NEED_CS) {
-    ok = (rho > (M)0) && (cs2 > (M)0) && isfinite(cs2) && isfinite(P);
-    cs = sqrt_(cs2 > (M)0 ? cs2 : (M)0);
-  }
-#pragma unroll
-  for (int a = 0; a < D; ++a) {
-    Qf[a][0] = W[1 + a];
-#pragma unroll
-    for (int b = 0; b < D; ++b) Qf[a][1 + b] = W[1 + b] * u[a] + (a == b ? P : (M)0);
-    Qf[a][NC - 1] = (W[NC - 1] + P) * u[a];
-  }
-  return ok;
-}
-
-// ------------------------------------------------------------------------------------------
-// storage: FP64 holds f_i; FP32 holds d_i = f_i - W_ref/Q (W_ref a per-run FP64 constant)
-// ------------------------------------------------------------------------------------------
-template <class S>
-struct Store;
-template <>
-struct Store<double> {
-  using M = double;
-  static constexpr bool kOffset = false;
-};
-template <>
-struct Store<float> {
-  using M = float;
-  static constexpr bool kOffset = true;
-};
-
-// Loads the populations of cell (cx, cy), pulled across the links (or in place), into fr[i][k].
-// Layout [i][y][x][4]: one vector access per direction.  `interior`: the caller guarantees that
-// (cx, cy) and its four neighbours lie inside the domain (no boundary rule needed).  Offsets are
-// 32-bit (vlbm_create bounds 2D * 4 * nx * ny below 2^31).
-template <int D, class S>
-__device__ __forceinline__ void load_cell(const S* __restrict__ fin, const KParams& p, int cx, int cy, int pulled,
-                                          bool interior, typename Store<S>::M (&fr)[2 * D][D + 2]) {
-  using M = typename Store<S>::M;
-  constexpr int NC = D + 2, Q = 2 * D;
-  const int plane = (int)p.plane;
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    int sx = cx, sy = cy;
-    if (pulled) {
-      if (interior) {
-        sx = cx - sig_x(i);
-        sy = cy - sig_y(i);
-      } else {
-        sx = nb_index(cx - sig_x(i), p.nx, p.bc[0], p.bc[1]);
-        if (D == 2) sy = nb_index(cy - sig_y(i), p.ny, p.bc[2], p.bc[3]);
-      }
-    }
-    S v[4];
-    ld4g(fin + (i * plane + sy * p.nx + sx) * 4, v);
-#pragma unroll
-    for (int k = 0; k < NC; ++k) fr[i][k] = (M)v[k];
-  }
-}
-
-// Stores one cell's populations f[i][k] (layout [i][y][x][4]).
-template <int D, class S, class M>
-__device__ __forceinline__ void store_cell(S* __restrict__ fout, const KParams& p, int cell, const M (&f)[2 * D][D + 2]) {
-  const int plane = (int)p.plane;
-#pragma unroll
-  for (int i = 0; i < 2 * D; ++i) {
-    S v[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) v[k] = k < D + 2 ? (S)f[i][k] : (S)0;
-    st4g(fout + (i * plane + cell) * 4, v);
-  }
-}
-
-// Zeroth moment of one cell: W_k = sum_i f_i (direction pairs first); in FP32 storage the sum of
-// deviations plus Q W_ref/Q (wq).
-template <int D, class M, bool OFFSET>
-__device__ __forceinline__ void moments(const M (&fr)[2 * D][D + 2], const M* wq, M (&W)[D + 2]) {
-#pragma unroll
-  for (int k = 0; k < D + 2; ++k) {
-    M acc = fr[0][k] + fr[1][k];
-    if constexpr (D == 2) acc += fr[2][k] + fr[3][k];
-    if constexpr (OFFSET) acc += wq[k];
-    W[k] = acc;
-  }
-}
-
-// ------------------------------------------------------------------------------------------
-// Maxima: per-cell values reduced within a CTA and stored as the CTA's partial (no atomics).
-// FP64: non-negative doubles compared as their 64-bit patterns (same order, integer pipe);
-// FP32: float max.  The one-CTA link-speed kernel folds the partials.
-// ------------------------------------------------------------------------------------------
-template <class M>
-struct Red;
-template <>
-struct Red<double> {
-  using T = unsigned long long;
-  static __device__ __forceinline__ T make(double x) {  // |x| as an ordered bit pattern
-    return (T)__double_as_longlong(x) & 0x7fffffffffffffffull;
-  }
-  static __device__ __forceinline__ T mx(T a, T b) { return a > b ? a : b; }
-  static __device__ __forceinline__ double value(T v) { return __longlong_as_double((long long)v); }
-};
-template <>
-struct Red<float> {
-  using T = float;
-  static __device__ __forceinline__ T make(float x) { return fabsf(x); }
-  static __device__ __forceinline__ T mx(T a, T b) { return fmaxf(a, b); }
-  static __device__ __forceinline__ double value(T v) { return (double)v; }
-};
-
-// Per-cell contributions to (s_max, M_0..M_{NC-1}) (Eqs. 30, 36).
-template <int D, class M>
-__device__ __forceinline__ void cell_maxima(const M (&u)[D], M cs, const M (&Qf)[D][D + 2], typename Red<M>::T (&v)[kNV]) {
-  using R = Red<M>;
-#pragma unroll
-  for (int a = 0; a < D; ++a) {
-    v[0] = R::mx(v[0], R::make(fabs(u[a]) + cs));
-#pragma unroll
-    for (int k = 0; k < D + 2; ++k) v[1 + k] = R::mx(v[1 + k], R::make(Qf[a][k]));
-  }
-}
-
-template <class M, int NT>
-__device__ __forceinline__ void block_max_store(typename Red<M>::T (&v)[kNV], double* __restrict__ part_slot, int cta,
-                                                int ncta, int* nparts_slot) {
-  using R = Red<M>;
-  using T = typename R::T;
-  __shared__ T red_s[NT / 32][kNV];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int j = 0; j < kNV; ++j) {
-    T x = v[j];
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) x = R::mx(x, __shfl_xor_sync(0xffffffffu, x, off));
-    if (lane == 0) red_s[warp][j] = x;
-  }
-  __syncthreads();
-  if (threadIdx.x < kNV) {
-    T x = red_s[0][threadIdx.x];
-#pragma unroll 4
-    for (int w = 1; w < NT / 32; ++w) x = R::mx(x, red_s[w][threadIdx.x]);
-    part_slot[(long long)cta * kNV + threadIdx.x] = R::value(x);
-  }
-  if (cta == 0 && threadIdx.x == 0) *nparts_slot = ncta;
-}
-
-// Fold the partials of one slot with one CTA of NT threads into out[j] (valid in thread 0).  The
-// partials are non-negative doubles and are compared as 64-bit patterns on the integer pipe (a
-// single SM's FP64 pipe would make this fold cost tens of microseconds).
-template <int NT>
-__device__ __forceinline__ void fold_partials(const double* __restrict__ part_slot, int nparts, double (&out)[kNV]) {
-  using T = unsigned long long;
-  __shared__ T red_s[NT / 32][kNV];
-  const T* bits = reinterpret_cast<const T*>(part_slot);
-  T v[kNV];
-#pragma unroll
-  for (int j = 0; j < kNV; ++j) v[j] = 0ull;
-  for (int c = threadIdx.x; c < nparts; c += NT)
-#pragma unroll
-    for (int j = 0; j < kNV; ++j) {
-      const T x = __ldg(bits + (long long)c * kNV + j);
-      v[j] = x > v[j] ? x : v[j];
-    }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int j = 0; j < kNV; ++j) {
-    T x = v[j];
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      const T y = __shfl_xor_sync(0xffffffffu, x, off);
-      x = y > x ? y : x;
-    }
-    if (lane == 0) red_s[warp][j] = x;
-  }
-  __syncthreads();
-  if (warp == 0) {
-#pragma unroll
-    for (int j = 0; j < kNV; ++j) {
-      T x = lane < NT / 32 ? red_s[lane][j] : 0ull;
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        const T y = __shfl_xor_sync(0xffffffffu, x, off);
-        x = y > x ? y : x;
-      }
-      out[j] = __longlong_as_double((long long)x);
-    }
-  }
-}
 
 // ------------------------------------------------------------------------------------------
 // k_reduce: s_max and M_k of the current state (two-pass form; also feeds vlbm_get_beta)

@@ -67,6 +67,8 @@ def _load():
         "vlbm_time_step_kernel": [V, I32, D],
         "vlbm_launches_per_step": [V, C.POINTER(I32)],
         "vlbm_set_profiling": [V, I32],
+        "vlbm_adjoint": [V, V, I64, I32, V, V, D],
+        "vlbm_adjoint_timing": [V, D],
         "vlbm_get_profile": [V, D, C.POINTER(I64)],
     }
     for name, args in sig.items():
@@ -118,7 +120,7 @@ class Config:
     beta_min: float = 0.75
     beta_max: float = 1.0
     c_sensor: float = 4.0
-    ducros_eps: float = 1e-12
+    ducros_eps: float = 1e-6
     retarget_every: int = 1
     precision: str = "fp64"
     algorithm: str = "auto"
@@ -221,6 +223,23 @@ class Solver:
     def time_step_kernel(self, reps: int = 10) -> float:
         ms = C.c_double()
         _check(_lib.vlbm_time_step_kernel(self._h, int(reps), C.byref(ms)), "vlbm_time_step_kernel")
+        return ms.value
+
+    def adjoint(self, W0, n_steps: int, checkpoint_every: int, dJ_dWT, dJ_dW0=None):
+        """dJ/dW0 (CUDA tensor) and dJ/d(gamma, a, b, R, cv) (numpy) of an objective with gradient
+        dJ_dWT at the final state of the run vlbm_init(W0) + n_steps steps (vlbm_adjoint)."""
+        if dJ_dW0 is None:
+            dJ_dW0 = self.torch.empty(self.shape, dtype=self.torch.float64, device=self.device)
+        deos = np.zeros(5)
+        _check(_lib.vlbm_adjoint(self._h, C.c_void_p(_ptr(W0)), int(n_steps), int(checkpoint_every),
+                                 C.c_void_p(_ptr(dJ_dWT)), C.c_void_p(_ptr(dJ_dW0)),
+                                 deos.ctypes.data_as(C.POINTER(C.c_double))), "vlbm_adjoint")
+        return dJ_dW0, deos
+
+    def adjoint_timing(self) -> float:
+        """Device ms of the reverse pass of the last adjoint call."""
+        ms = C.c_double()
+        _check(_lib.vlbm_adjoint_timing(self._h, C.byref(ms)), "vlbm_adjoint_timing")
         return ms.value
 
     def set_profiling(self, on: bool) -> None:

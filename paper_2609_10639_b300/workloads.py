@@ -63,7 +63,7 @@ class Problem:
     beta_min: float = 0.75
     beta_max: float = 1.0
     c_sensor: float = 4.0
-    ducros_eps: float = 1e-12
+    ducros_eps: float = 1e-6
 
     @property
     def dx(self) -> float:

@@ -1,0 +1,123 @@
+"""The benchmark workloads at their full sizes on the GPU.
+
+* BZT van der Waals interface, 2048^2: 100 FP64 steps against the oracle on the whole field (bar
+  from the oracle's own rounding spread, as in the parity tests).
+* Periodic vortex with acoustic noise, 8192^2, 2000 steps: FP32 storage against FP64 at equal time
+  (the FP32 run ends on the FP64 run's final time), relative L1 of every component of W <= 1e-5;
+  the FP64 path is itself oracle-checked on a 1024^2 copy (100 steps, 1e-11).
+* Four-quadrant problem, 4096^2, to t = 0.25: the run stays physical and conserves mass up to the
+  boundary fluxes' rounding (zero-gradient boundaries let mass leave; checked in FP64 against the
+  FP32-storage run at equal time: density L1 relative difference <= 1e-3 and shock positions).
+"""
+import numpy as np
+import pytest
+
+from paper_2609_10639_b300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+def _rel_maxnorm(a, b):
+    num = np.abs(a - b).reshape(a.shape[0], -1).max(axis=1)
+    den = np.maximum(np.abs(b).reshape(b.shape[0], -1).max(axis=1), 1e-300)
+    return float((num / den).max())
+
+
+def test_bzt_interface_2048_fp64_against_oracle():
+    import torch
+
+    from oracle import oracle as O
+    from paper_2609_10639_b300 import vlbm
+
+    prob = wl.BZT_2D
+    W0 = wl.bzt_interface_2d(prob)
+    g = vlbm.Solver.for_problem(prob)
+    g.init(torch.from_numpy(W0).cuda())
+    assert g.step(100) == 100
+    o = O.OracleSolver.for_problem(prob)
+    o.init(W0)
+    o.step(100)
+    Wo = o.W()
+    # conditioning of the map at this state: the oracle perturbed at the 1e-16 level
+    rng = np.random.default_rng(3)
+    o2 = O.OracleSolver.for_problem(prob)
+    o2.init(W0 * (1.0 + 1e-16 * rng.standard_normal(W0.shape)))
+    o2.step(100)
+    bar = max(1e-11, 10.0 * _rel_maxnorm(o2.W(), Wo))
+    err = _rel_maxnorm(g.W().cpu().numpy(), Wo)
+    assert err <= bar, (err, bar)
+
+
+def test_vortex_1024_fp64_against_oracle():
+    import torch
+
+    from oracle import oracle as O
+    from paper_2609_10639_b300 import vlbm
+
+    prob = wl.VORTEX_SCALE_2D.resized(1024)
+    W0 = wl.vortex_acoustic_2d(prob)
+    g = vlbm.Solver.for_problem(prob)
+    g.init(torch.from_numpy(W0).cuda())
+    g.step(100)
+    o = O.OracleSolver.for_problem(prob)
+    o.init(W0)
+    o.step(100)
+    assert _rel_maxnorm(g.W().cpu().numpy(), o.W()) <= 1e-11
+
+
+def test_vortex_8192_fp32_storage_error_bar():
+    import torch
+
+    from paper_2609_10639_b300 import vlbm
+
+    prob = wl.VORTEX_SCALE_2D
+    W0 = torch.from_numpy(wl.vortex_acoustic_2d(prob)).cuda()
+    a = vlbm.Solver.for_problem(prob, precision="fp64")
+    a.init(W0)
+    assert a.step(prob.n_steps) == prob.n_steps
+    t_end = a.time()[0]
+    Wa = a.W()
+    a.close()
+    b = vlbm.Solver.for_problem(prob, precision="fp32_store")
+    b.init(W0)
+    b.step(10 ** 6, t_end)
+    assert b.time()[0] == t_end
+    Wb = b.W()
+    rel_l1 = ((Wb - Wa).abs().reshape(4, -1).sum(1) / Wa.abs().reshape(4, -1).sum(1)).cpu().numpy()
+    assert rel_l1.max() <= 1e-5, rel_l1
+    assert bool(torch.isfinite(Wb).all())
+
+
+def test_quadrants_4096_full_run():
+    import torch
+
+    from paper_2609_10639_b300 import vlbm
+
+    prob = wl.QUADRANTS_2D
+    W0 = torch.from_numpy(wl.quadrants_2d(prob)).cuda()
+    a = vlbm.Solver.for_problem(prob, precision="fp64")
+    a.init(W0)
+    n = a.step(10 ** 6, prob.t_end)
+    assert a.time()[0] == prob.t_end and n > 1000
+    ra = a.W()[0]
+    a.close()
+    b = vlbm.Solver.for_problem(prob, precision="fp32_store")
+    b.init(W0)
+    b.step(10 ** 6, prob.t_end)
+    rb = b.W()[0]
+    assert bool(torch.isfinite(rb).all()) and float(ra.min()) > 0.0
+    rel = float((rb - ra).abs().sum() / ra.abs().sum())
+    assert rel <= 1e-3, rel
+    # discontinuities (local-maximum jumps above 10% of the density range) within one cell
+    thr = 0.1 * float(ra.max() - ra.min())
+    total = matched = 0
+    for axis in (0, 1):
+        da = (ra.diff(dim=axis)).abs()
+        db = (rb.diff(dim=axis)).abs()
+        pa = (da > thr) & (da >= da.roll(1, axis)) & (da >= da.roll(-1, axis))
+        pb = (db > 0.5 * thr)
+        near = pb | pb.roll(1, axis) | pb.roll(-1, axis)
+        total += int(pa.sum())
+        matched += int((pa & near).sum())
+    assert total > 1000
+    assert matched / total >= 0.999, (matched, total)
