@@ -74,6 +74,11 @@ typedef struct {
 typedef enum { VLBM_FP64 = 0, VLBM_FP32_STORE = 1 } vlbm_precision;
 typedef enum { VLBM_BETA_SENSOR = 0, VLBM_BETA_CONST = 1 } vlbm_beta_mode;
 typedef enum { VLBM_ALGO_AUTO = 0, VLBM_ALGO_TWO_PASS = 1, VLBM_ALGO_LOOKAHEAD = 2 } vlbm_algorithm;
+/* How a 2D step kernel covers the grid: VLBM_TILING_STRIP walks a CTA down a column strip with
+ * ring buffers (each quantity computed once per row; the default in 2D), VLBM_TILING_TILE computes
+ * each 32 x 16 tile with its own halo.  Both give the same results up to rounding order; 1D
+ * always uses tiles. */
+typedef enum { VLBM_TILING_AUTO = 0, VLBM_TILING_TILE = 1, VLBM_TILING_STRIP = 2 } vlbm_tiling;
 
 typedef struct {
   double cfl;             /* target Courant number in (0, 1) (Eq. 37)                           */
@@ -87,6 +92,7 @@ typedef struct {
   int32_t retarget_every; /* retarget the link speed every k >= 1 steps (Sec. III E)            */
   int32_t precision;      /* vlbm_precision: FP64 populations, or FP32 storage of deviations    */
   int32_t algorithm;      /* vlbm_algorithm: how the two global maxima of a step are obtained   */
+  int32_t tiling;         /* vlbm_tiling: how the 2D step kernel covers the grid                */
 } vlbm_params;
 
 /* Creates a solver for the grid, EOS and parameters, bound to `cuda_stream` (a cudaStream_t, or
@@ -140,6 +146,25 @@ vlbm_status vlbm_get_dt_history(vlbm_t h, double* dt_host, double* c_host, int64
  * returns to the adaptive rule.  Steps beyond the sequence fail with VLBM_E_INVAL.  Used to repeat
  * a recorded run exactly (finite differences, adjoint). */
 vlbm_status vlbm_set_dt_schedule(vlbm_t h, const double* c_host, int64_t n);
+
+/* Domain totals sum_x W_k(x) of the current state, k = 0..D+1 (mass, momentum, total energy per
+ * unit cell volume), summed in FP64 with Neumaier compensation in a fixed order, written to the
+ * host array totals[D+2] (synchronises).  On periodic domains the step conserves them up to
+ * rounding (Sec. III A: the collision conserves W and streaming moves populations without loss);
+ * zero-gradient sides let the boundary fluxes change them. */
+vlbm_status vlbm_get_totals(vlbm_t h, double* totals);
+
+/* Checkpoint / resume of a run.  vlbm_save_state writes the complete state (populations in
+ * their storage precision, device scalars: time, step counter, link speed, FP32 reference share,
+ * and the (dt, c) history) into the host buffer `host` of `cap` bytes and the size to *used;
+ * host == NULL only queries the size.  The buffer ends with a 64-bit checksum.  It synchronises
+ * and fails with VLBM_E_INVAL when cap is too small.  vlbm_load_state restores such a buffer
+ * (n_bytes long) into a handle created with the same grid, lattice and precision (else
+ * VLBM_E_INVAL; a damaged buffer gives VLBM_E_CHECKSUM); stepping then continues exactly as the
+ * saving handle would have.  A replay schedule (vlbm_set_dt_schedule) belongs to the handle and
+ * is not part of the state. */
+vlbm_status vlbm_save_state(vlbm_t h, void* host, size_t cap, size_t* used);
+vlbm_status vlbm_load_state(vlbm_t h, const void* host, size_t n_bytes);
 
 /* Launches the dominant step kernel `reps` times on the handle's stream (without advancing the
  * state: each launch recomputes the same next state into the spare buffer) bracketed by CUDA

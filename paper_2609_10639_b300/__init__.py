@@ -5,4 +5,4 @@ is its Python binding, `workloads` builds seeded synthetic inputs.  Importing `v
 the built library; there is no CPU fallback.
 """
 
-__all__ = ["vlbm", "workloads"]
+__all__ = ["vlbm", "workloads", "autograd"]

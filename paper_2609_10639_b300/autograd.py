@@ -11,7 +11,7 @@ from . import vlbm
 EOS_KEYS = ("gamma", "a", "b", "R", "cv")
 
 
-class VLBMRun(torch.autograd.Function):
+class VLBMFunction(torch.autograd.Function):
     """forward(W0, eos_param, cfg, n_steps, checkpoint_every, param_name) -> W(T).
 
     W0: CUDA float64 tensor (D+2, ny, nx); eos_param: 0-d float64 tensor holding the EOS parameter
@@ -43,4 +43,4 @@ class VLBMRun(torch.autograd.Function):
 
 
 def run(W0, eos_param, cfg: vlbm.Config, n_steps: int, checkpoint_every: int = 32, param_name: str = "gamma"):
-    return VLBMRun.apply(W0, eos_param, cfg, n_steps, checkpoint_every, param_name)
+    return VLBMFunction.apply(W0, eos_param, cfg, n_steps, checkpoint_every, param_name)

@@ -248,6 +248,39 @@ __device__ __forceinline__ void moments(const M (&fr)[2 * D][D + 2], const M* wq
   }
 }
 
+// Fused reprojection (c_old -> c_new, Eqs. 38-40) and relaxation (Eqs. 20, 22) of one cell:
+//   f*_{a,+-} = W/Q  +-  [ beta Q_a / c + (1 - 2 beta) r (f_{a+} - f_{a-}) / 2 ]
+//               (+ for x, - for y)  (1 - 2 beta) r^2 ((f_x+ + f_x-) - (f_y+ + f_y-)) / 4   (D2Q4 K-term),
+// r = c_old / c_new.  In FP32 storage the same update acts on the deviations (W/Q -> dW/Q).
+template <int D, class M>
+__device__ __forceinline__ void relax_cell(M (&f)[2 * D][D + 2], const M (&Qc)[D][D + 2], M beta, M r, M inv_c) {
+  constexpr int NC = D + 2;
+  const M om = (M)1 - (M)2 * beta;
+  const M bq = beta * inv_c;
+  const M omr = om * r * (M)0.5;
+  const M omk = om * r * r * (M)0.25;
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    const M sx = f[0][k] + f[1][k];
+    const M gx = bq * Qc[0][k] + omr * (f[1][k] - f[0][k]);
+    if constexpr (D == 1) {
+      const M w = sx * (M)0.5;
+      f[0][k] = w - gx;
+      f[1][k] = w + gx;
+    } else {
+      const M sy = f[2][k] + f[3][k];
+      const M w = (sx + sy) * (M)0.25;
+      const M gy = bq * Qc[1][k] + omr * (f[3][k] - f[2][k]);
+      const M kk = omk * (sx - sy);
+      const M wx = w + kk, wy = w - kk;
+      f[0][k] = wx - gx;
+      f[1][k] = wx + gx;
+      f[2][k] = wy - gy;
+      f[3][k] = wy + gy;
+    }
+  }
+}
+
 // ------------------------------------------------------------------------------------------
 // Maxima: per-cell values reduced within a CTA and stored as the CTA's partial (no atomics).
 // FP64: non-negative doubles compared as their 64-bit patterns (same order, integer pipe);

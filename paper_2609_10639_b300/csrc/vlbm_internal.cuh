@@ -64,6 +64,7 @@ struct KParams {
   double beta_const, beta_min, beta_max, c_sensor, ducros_eps;
   int retarget_every;
   int max_parts;    // capacity of one partial-maxima slot (CTAs of the largest producer)
+  int strip;        // 2D step kernel: column-strip form (1) or tiles (0)
   Coef<double> cd;
   Coef<float> cf;
 };
@@ -80,7 +81,9 @@ struct Launch {
 };
 
 // precision: 0 = FP64, 1 = FP32 storage.  lookahead: fused single-kernel step.
-cudaError_t launch_reduce(const Launch& L, int precision, const void* fin, int pulled);
+// in_run: the reduction is a step of a run and is skipped once the run is done or failed;
+// otherwise (beta readback, state restore) it always runs.
+cudaError_t launch_reduce(const Launch& L, int precision, const void* fin, int pulled, bool in_run);
 cudaError_t launch_dt(const Launch& L);
 cudaError_t launch_step(const Launch& L, int precision, bool lookahead, const void* fin, void* fout, int pulled);
 cudaError_t launch_beta(const Launch& L, int precision, const void* fin, int pulled, double* beta_out);
@@ -88,7 +91,15 @@ cudaError_t launch_init(const Launch& L, int precision, const double* W0, void* 
 cudaError_t launch_get_W(const Launch& L, int precision, const void* fin, int pulled, double* W);
 cudaError_t launch_get_f(const Launch& L, int precision, const void* fin, int pulled, double* f);
 cudaError_t launch_begin(const Launch& L, double t_end);
+// Compensated domain totals sum_x W_k into out[0..nc) (W: nc planes of scratch, partial: per-block
+// sums of sum_blocks() blocks).
+cudaError_t launch_totals(const Launch& L, int precision, const void* fin, int pulled, double* W, double* partial,
+                          int nblk_sum, double* out);
 cudaError_t prepare_kernels();
+// Column-strip form of the 2D step kernel (vlbm_roll.cu).
+cudaError_t launch_roll(const Launch& L, int precision, bool lookahead, const void* fin, void* fout, int pulled);
+cudaError_t prepare_roll_kernels();
+long long roll_ctas(const KParams& p);
 int sum_blocks(const KParams& p);
 int max_partials(const KParams& p);
 

@@ -40,11 +40,11 @@ namespace vlbm {
 // ------------------------------------------------------------------------------------------
 template <int D, class S, int NT>
 __global__ void __launch_bounds__(NT) k_reduce(const S* __restrict__ fin, Scalars* __restrict__ sc, const KParams p,
-                                                const int pulled, double* __restrict__ part) {
+                                                const int pulled, double* __restrict__ part, const int in_run) {
   using M = typename Store<S>::M;
   using R = Red<M>;
   constexpr int NC = D + 2;
-  if (sc->done || sc->err) return;
+  if (in_run && (sc->done || sc->err)) return;  // a finished or failed run skips its remaining steps
   const int slot = (int)(sc->n & 1);
   M wq[NC];
 #pragma unroll
@@ -173,39 +173,6 @@ __device__ __forceinline__ M sensor_beta(const KParams& p, const Coef<M>& c, con
   M chi = c.c_sensor * sbar * tbar;
   chi = chi <= (M)0 ? (M)0 : (chi >= (M)1 ? (M)1 : chi);
   return c.beta_max - c.dbeta * chi;
-}
-
-// Fused reprojection (c_old -> c_new, Eqs. 38-40) and relaxation (Eqs. 20, 22) of one cell:
-//   f*_{a,+-} = W/Q  +-  [ beta Q_a / c + (1 - 2 beta) r (f_{a+} - f_{a-}) / 2 ]
-//               (+ for x, - for y)  (1 - 2 beta) r^2 ((f_x+ + f_x-) - (f_y+ + f_y-)) / 4   (D2Q4 K-term),
-// r = c_old / c_new.  In FP32 storage the same update acts on the deviations (W/Q -> dW/Q).
-template <int D, class M>
-__device__ __forceinline__ void relax_cell(M (&f)[2 * D][D + 2], const M (&Qc)[D][D + 2], M beta, M r, M inv_c) {
-  constexpr int NC = D + 2;
-  const M om = (M)1 - (M)2 * beta;
-  const M bq = beta * inv_c;
-  const M omr = om * r * (M)0.5;
-  const M omk = om * r * r * (M)0.25;
-#pragma unroll
-  for (int k = 0; k < NC; ++k) {
-    const M sx = f[0][k] + f[1][k];
-    const M gx = bq * Qc[0][k] + omr * (f[1][k] - f[0][k]);
-    if constexpr (D == 1) {
-      const M w = sx * (M)0.5;
-      f[0][k] = w - gx;
-      f[1][k] = w + gx;
-    } else {
-      const M sy = f[2][k] + f[3][k];
-      const M w = (sx + sy) * (M)0.25;
-      const M gy = bq * Qc[1][k] + omr * (f[3][k] - f[2][k]);
-      const M kk = omk * (sx - sy);
-      const M wx = w + kk, wy = w - kk;
-      f[0][k] = wx - gx;
-      f[1][k] = wx + gx;
-      f[2][k] = wy - gy;
-      f[3][k] = wy + gy;
-    }
-  }
 }
 
 template <int D, class S, bool LOOK, bool BETA_OUT, int TX, int TY>
@@ -366,9 +333,7 @@ __global__ void __launch_bounds__(TX * TY) k_tile(const S* __restrict__ fin, S* 
     const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
     const int gx = x0 + tx, gy = y0 + ty;
     if (gx < p.nx && gy < p.ny) {
-      M W[NC];
-#pragma unroll
-      for (int k = 0; k < NC; ++k) W[k] = wq[k];
+      M fr[Q][NC], W[NC];
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
         const int qx = centre_pos(gx - sig_x(i), p.nx, p.bc[0], p.bc[1]) - (x0 - RB);
@@ -376,8 +341,11 @@ __global__ void __launch_bounds__(TX * TY) k_tile(const S* __restrict__ fin, S* 
         M v[4];
         ld4s(s_f + (i * BY * BX + qy * BX + qx) * 4, v);
 #pragma unroll
-        for (int k = 0; k < NC; ++k) W[k] += v[k];
+        for (int k = 0; k < NC; ++k) fr[i][k] = v[k];
       }
+      // same summation order as every other moment evaluation (the maxima are those k_reduce
+      // would compute from the stored state)
+      moments<D, M, OFF>(fr, wq, W);
       M u[D], Qf[D][NC], cs;
       bad = !prim_flux<D, M, true>(p, W, u, Qf, cs);
       cell_maxima<D, M>(u, cs, Qf, v);
@@ -465,6 +433,21 @@ __global__ void k_sum_final(const double* __restrict__ partial, int nblk, const 
     }
     sc->wref[k] = (S + Cc) / (double)p.plane / (double)p.q;
     sc->wq_f[k] = (float)(p.q * sc->wref[k]);
+  }
+}
+
+// Domain totals sum_x W_k of the current state: the per-block partials of k_sum_partial folded in
+// block order with the same compensation (the discrete conservation law of the step, Sec. III A).
+__global__ void k_sum_out(const double* __restrict__ partial, int nblk, const KParams p, double* __restrict__ out) {
+  for (int k = 0; k < p.nc; ++k) {
+    double S = 0.0, Cc = 0.0;
+    for (int b = 0; b < nblk; ++b) {
+      const double x = partial[b * 4 + k];
+      const double t = S + x;
+      Cc += fabs(S) >= fabs(x) ? (S - t) + x : (x - t) + S;
+      S = t;
+    }
+    out[k] = S + Cc;
   }
 }
 
@@ -642,8 +625,8 @@ unsigned blocks_gs(const KParams& p) {
 }
 
 template <int D, class S>
-void launch_reduce_t(const Launch& L, const void* fin, int pulled) {
-  k_reduce<D, S, kNT1><<<blocks_gs(*L.p), kNT1, 0, L.stream>>>((const S*)fin, L.sc, *L.p, pulled, L.part);
+void launch_reduce_t(const Launch& L, const void* fin, int pulled, int in_run) {
+  k_reduce<D, S, kNT1><<<blocks_gs(*L.p), kNT1, 0, L.stream>>>((const S*)fin, L.sc, *L.p, pulled, L.part, in_run);
 }
 }  // namespace
 
@@ -658,6 +641,7 @@ cudaError_t prepare_kernels() {
   VLBM_PREP(2, double, false, false) VLBM_PREP(2, double, true, false) VLBM_PREP(2, double, false, true)
   VLBM_PREP(2, float, false, false) VLBM_PREP(2, float, true, false) VLBM_PREP(2, float, false, true)
 #undef VLBM_PREP
+  if (e == cudaSuccess) e = prepare_roll_kernels();
   return e;
 }
 
@@ -671,16 +655,19 @@ int max_partials(const KParams& p) {
   long long tiles = p.dim == 2 ? (long long)((p.nx + TileCfg<2>::TX - 1) / TileCfg<2>::TX) * ((p.ny + TileCfg<2>::TY - 1) / TileCfg<2>::TY)
                                : (long long)((p.nx + TileCfg<1>::TX - 1) / TileCfg<1>::TX);
   long long gs = blocks_gs(p);
-  return (int)(tiles > gs ? tiles : gs);
+  long long m = tiles > gs ? tiles : gs;
+  const long long rc = roll_ctas(p);
+  return (int)(rc > m ? rc : m);
 }
 
-cudaError_t launch_reduce(const Launch& L, int precision, const void* fin, int pulled) {
+cudaError_t launch_reduce(const Launch& L, int precision, const void* fin, int pulled, bool in_run) {
+  const int r = in_run ? 1 : 0;
   if (L.p->dim == 1) {
-    if (precision == 0) launch_reduce_t<1, double>(L, fin, pulled);
-    else launch_reduce_t<1, float>(L, fin, pulled);
+    if (precision == 0) launch_reduce_t<1, double>(L, fin, pulled, r);
+    else launch_reduce_t<1, float>(L, fin, pulled, r);
   } else {
-    if (precision == 0) launch_reduce_t<2, double>(L, fin, pulled);
-    else launch_reduce_t<2, float>(L, fin, pulled);
+    if (precision == 0) launch_reduce_t<2, double>(L, fin, pulled, r);
+    else launch_reduce_t<2, float>(L, fin, pulled, r);
   }
   return cudaGetLastError();
 }
@@ -691,6 +678,7 @@ cudaError_t launch_dt(const Launch& L) {
 }
 
 cudaError_t launch_step(const Launch& L, int precision, bool lookahead, const void* fin, void* fout, int pulled) {
+  if (L.p->dim == 2 && L.p->strip) return launch_roll(L, precision, lookahead, fin, fout, pulled);
   const char* base = reinterpret_cast<const char*>(L.sc);
   if (precision == 0) {
     const void* invM = base + offsetof(Scalars, inv_M);
@@ -706,7 +694,7 @@ cudaError_t launch_beta(const Launch& L, int precision, const void* fin, int pul
   const KParams& p = *L.p;
   // maxima of the current state into partial slot n & 1 (the same values any producer of that
   // slot writes for this state), then 1/M_k into the beta scratch
-  cudaError_t e = launch_reduce(L, precision, fin, pulled);
+  cudaError_t e = launch_reduce(L, precision, fin, pulled, false);
   if (e != cudaSuccess) return e;
   double* invM_beta = beta_out + p.plane;  // caller provides plane + 8 doubles (1/M_k in FP64, FP32)
   k_beta_prep<<<1, kNTD, 0, L.stream>>>(L.sc, p, L.part, invM_beta);
@@ -757,6 +745,16 @@ cudaError_t launch_get_f(const Launch& L, int precision, const void* fin, int pu
     if (precision == 0) k_get_f<2, double, kNT1><<<blocks1(p), kNT1, 0, L.stream>>>((const double*)fin, L.sc, p, pulled, f);
     else k_get_f<2, float, kNT1><<<blocks1(p), kNT1, 0, L.stream>>>((const float*)fin, L.sc, p, pulled, f);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_totals(const Launch& L, int precision, const void* fin, int pulled, double* W, double* partial,
+                          int nblk_sum, double* out) {
+  const KParams& p = *L.p;
+  cudaError_t e = launch_get_W(L, precision, fin, pulled, W);
+  if (e != cudaSuccess) return e;
+  k_sum_partial<kNT1><<<nblk_sum, kNT1, 0, L.stream>>>(W, p, partial);
+  k_sum_out<<<1, 1, 0, L.stream>>>(partial, nblk_sum, p, out);
   return cudaGetLastError();
 }
 
@@ -891,8 +889,8 @@ extern "C" vlbm_status vlbm_beta_noalloc(const vlbm_grid* grid, const vlbm_eos* 
   // The scalar block must start at zero (no error bit, step 0); the partials and 1/M_k are
   // fully written by this call before they are read.
   if (cudaMemsetAsync(sc, 0, sizeof(Scalars), s) != cudaSuccess) return VLBM_E_CUDA;
-  if (p.dim == 1) k_reduce<1, double, kNoallocCtaCells><<<ncta, kNoallocCtaCells, 0, s>>>(f, sc, p, pulled, part);
-  else k_reduce<2, double, kNoallocCtaCells><<<ncta, kNoallocCtaCells, 0, s>>>(f, sc, p, pulled, part);
+  if (p.dim == 1) k_reduce<1, double, kNoallocCtaCells><<<ncta, kNoallocCtaCells, 0, s>>>(f, sc, p, pulled, part, 0);
+  else k_reduce<2, double, kNoallocCtaCells><<<ncta, kNoallocCtaCells, 0, s>>>(f, sc, p, pulled, part, 0);
   k_beta_prep<<<1, kNTD, 0, s>>>(sc, p, part, invM);
   if (p.dim == 1) {
     constexpr int TX = TileCfg<1>::TX, TY = TileCfg<1>::TY;

@@ -20,6 +20,7 @@ OK, E_INVAL, E_NOMEM, E_CUDA, E_NONPHYSICAL, E_TIMEOUT, E_STATE, E_CHECKSUM, E_U
 BC = {"periodic": 0, "zerograd": 1}
 PRECISION = {"fp64": 0, "fp32_store": 1}
 ALGORITHM = {"auto": 0, "two_pass": 1, "lookahead": 2}
+TILING = {"auto": 0, "tile": 1, "strip": 2}
 
 
 class VLBMError(RuntimeError):
@@ -45,7 +46,8 @@ class _Eos(C.Structure):
 class _Params(C.Structure):
     _fields_ = [("cfl", C.c_double), ("beta_mode", C.c_int32), ("beta_const", C.c_double), ("beta_min", C.c_double),
                 ("beta_max", C.c_double), ("c_sensor", C.c_double), ("ducros_eps", C.c_double),
-                ("retarget_every", C.c_int32), ("precision", C.c_int32), ("algorithm", C.c_int32)]
+                ("retarget_every", C.c_int32), ("precision", C.c_int32), ("algorithm", C.c_int32),
+                ("tiling", C.c_int32)]
 
 
 def _load():
@@ -70,6 +72,9 @@ def _load():
         "vlbm_adjoint": [V, V, I64, I32, V, V, D],
         "vlbm_adjoint_timing": [V, D],
         "vlbm_get_profile": [V, D, C.POINTER(I64)],
+        "vlbm_get_totals": [V, D],
+        "vlbm_save_state": [V, V, C.c_size_t, C.POINTER(C.c_size_t)],
+        "vlbm_load_state": [V, V, C.c_size_t],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -124,6 +129,7 @@ class Config:
     retarget_every: int = 1
     precision: str = "fp64"
     algorithm: str = "auto"
+    tiling: str = "auto"
 
 
 class Solver:
@@ -146,7 +152,8 @@ class Solver:
         else:
             eo = _Eos(1, 0.0, e["a"], e["b"], e["R"], e["cv"])
         p = _Params(cfg.cfl, 0 if cfg.beta_mode == "sensor" else 1, cfg.beta_const, cfg.beta_min, cfg.beta_max,
-                    cfg.c_sensor, cfg.ducros_eps, cfg.retarget_every, PRECISION[cfg.precision], ALGORITHM[cfg.algorithm])
+                    cfg.c_sensor, cfg.ducros_eps, cfg.retarget_every, PRECISION[cfg.precision], ALGORITHM[cfg.algorithm],
+                    TILING[cfg.tiling])
         h = C.c_void_p()
         _check(_lib.vlbm_create(C.byref(g), C.byref(eo), C.byref(p), C.c_void_p(self.stream.cuda_stream), C.byref(h)),
                "vlbm_create")
@@ -251,6 +258,25 @@ class Solver:
         _check(_lib.vlbm_get_profile(self._h, C.byref(ms), C.byref(n)), "vlbm_get_profile")
         return ms.value, n.value
 
+    def totals(self) -> np.ndarray:
+        """Compensated FP64 domain totals sum_x W_k of the current state (vlbm_get_totals)."""
+        out = np.zeros(self.nc)
+        _check(_lib.vlbm_get_totals(self._h, out.ctypes.data_as(C.POINTER(C.c_double))), "vlbm_get_totals")
+        return out
+
+    def save_state(self) -> bytes:
+        """The complete state of the run as a checksummed byte string (vlbm_save_state)."""
+        n = C.c_size_t()
+        _check(_lib.vlbm_save_state(self._h, None, 0, C.byref(n)), "vlbm_save_state")
+        buf = C.create_string_buffer(n.value)
+        _check(_lib.vlbm_save_state(self._h, buf, n.value, C.byref(n)), "vlbm_save_state")
+        return buf.raw
+
+    def load_state(self, state: bytes) -> None:
+        """Restores a state written by save_state on a solver of the same configuration."""
+        buf = C.create_string_buffer(bytes(state), len(state))
+        _check(_lib.vlbm_load_state(self._h, buf, len(state)), "vlbm_load_state")
+
     def launches_per_step(self) -> int:
         n = C.c_int32()
         _check(_lib.vlbm_launches_per_step(self._h, C.byref(n)), "vlbm_launches_per_step")
@@ -264,7 +290,8 @@ def _config_structs(cfg: Config):
     e = cfg.eos
     eo = _Eos(0, e["gamma"], 0.0, 0.0, 0.0, 0.0) if e["kind"] == "ideal" else _Eos(1, 0.0, e["a"], e["b"], e["R"], e["cv"])
     p = _Params(cfg.cfl, 0 if cfg.beta_mode == "sensor" else 1, cfg.beta_const, cfg.beta_min, cfg.beta_max,
-                cfg.c_sensor, cfg.ducros_eps, cfg.retarget_every, PRECISION[cfg.precision], ALGORITHM[cfg.algorithm])
+                cfg.c_sensor, cfg.ducros_eps, cfg.retarget_every, PRECISION[cfg.precision], ALGORITHM[cfg.algorithm],
+                    TILING[cfg.tiling])
     return g, eo, p
 
 

@@ -190,3 +190,33 @@ def test_fp32_storage_adjoint_against_fp64_adjoint():
         da, db = float((ga * vd).sum()), float((gb * vd).sum())
         assert abs(da - db) <= 1e-4 * abs(da), (da, db)
     assert abs(ea[0] - eb[0]) <= 1e-4 * abs(ea[0]), (ea[0], eb[0])
+
+
+def test_adjoint_vortex_128_twenty_directions():
+    # 128^2 periodic vortex, 200 steps, checkpoints every 32 steps: <dJ/dW0, v> against the dual
+    # numbers on the 20 seeded smooth directions, and dJ/dgamma.
+    import torch
+
+    from oracle import oracle as O
+    from paper_2609_10639_b300 import vlbm
+
+    prob = dataclasses.replace(wl.VORTEX_ADJOINT_2D.resized(128), n_steps=200)
+    W0 = wl.vortex_density_2d(prob)
+    g = wl.objective_weight(prob)
+    n = prob.n_steps
+    dJ = np.zeros_like(W0)
+    dJ[0] = g
+    s = vlbm.Solver.for_problem(prob)
+    dW0, deos = s.adjoint(torch.from_numpy(W0).cuda(), n, 32, torch.from_numpy(dJ).cuda())
+    dW0 = dW0.cpu().numpy()
+    o = O.OracleSolver.for_problem(prob)
+    o.init(W0)
+    c0 = o.time()[2]
+    o.step(n)
+    sched = np.concatenate([[c0], o.history()[1]])
+    for v in wl.directions(prob, count=20):
+        ref = _dual_dJ(prob, W0, n, g, sched, v=v)
+        got = float(np.sum(dW0 * v))
+        assert abs(got - ref) <= 1e-9 * abs(ref), (got, ref)
+    ref = _dual_dJ(prob, W0, n, g, sched, deos={"gamma": 1.0})
+    assert abs(deos[0] - ref) <= 1e-9 * abs(ref), (deos[0], ref)
