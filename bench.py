@@ -35,9 +35,11 @@ UNIT = "MLUPS"
 # Algorithmic bytes per cell update: every population read once and written once
 # (2D: 4 directions x 4 components x 2).
 BYTES_PER_CELL = {"fp64": 256, "fp32_store": 128}
-# Algorithmic FP64 floating-point operations per 2D cell update (ideal gas, shock sensor) of the
-# fused step, FMA counted as 2, divide and square root as 1 each (count in the design notes).
+# Algorithmic FP64 floating-point operations per 2D cell update (ideal gas, shock sensor), FMA
+# counted as 2, divide and square root as 1 each: 214 for the whole step, of which the step
+# kernel of the two-pass form performs 211 (the maxima pass adds c_s and the comparisons).
 FP64_FLOPS_PER_CELL = 214
+FP64_FLOPS_STEP_KERNEL = 211
 # Algorithmic bytes of one adjoint step including the recomputation of the forward state (FP64):
 # recompute 256 + read the forward state 128 + read lambda 128 + write lambda 128.
 ADJ_BYTES_PER_CELL = 640
@@ -107,6 +109,14 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def kernels_sha():
+    """Digest of the step-kernel sources (the counters in profiles/ are tied to it)."""
+    h = hashlib.sha256()
+    for name in ("vlbm_device.cuh", "vlbm_kernels.cu", "vlbm_roll.cu"):
+        h.update(open(os.path.join(ROOT, "paper_2609_10639_b300", "csrc", name), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def kernel_traffic(kind):
     """DRAM bytes per cell of the dominant kernel from the committed ncu summary, or None when the
     kernel source changed since the counters were taken."""
@@ -116,8 +126,7 @@ def kernel_traffic(kind):
         entry = d[kind]
     except Exception:
         return None
-    src = os.path.join(ROOT, "paper_2609_10639_b300", "csrc", "vlbm_kernels.cu")
-    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    digest = kernels_sha()
     if entry.get("kernels_sha") != digest:
         return None
     return float(entry["dram_bytes_per_cell"])
@@ -338,7 +347,7 @@ def run_ours(args):
     sm_mhz = clk.get("sm_mhz") or pk["sm_max_mhz"]
     k64_s = r64["kernel_ms_avg"] * 1e-3
     k32_s = r32["kernel_ms_avg"] * 1e-3
-    fp64_ach = FP64_FLOPS_PER_CELL * cells / k64_s / 1e12
+    fp64_ach = FP64_FLOPS_STEP_KERNEL * cells / k64_s / 1e12
     fp64_peak = fp64_peak_tflops(pk["sm_max_mhz"])
     hbm64 = BYTES_PER_CELL["fp64"] * cells / k64_s / 1e9
     hbm32 = BYTES_PER_CELL["fp32_store"] * cells / k32_s / 1e9
@@ -356,7 +365,8 @@ def run_ours(args):
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "alu", "achieved": fp64_ach, "peak": fp64_peak, "unit": "TFLOP/s",
                      "frac": fp64_ach / fp64_peak, "traffic": None if t64 is None else t64 * cells,
-                     "kernel": "k_tile<2,double> (FP64 step)", "kernel_ms": r64["kernel_ms_avg"],
+                     "kernel": "k_roll<double> (FP64 step kernel, column strips, two-pass form)",
+                     "kernel_ms": r64["kernel_ms_avg"], "flops_per_cell": FP64_FLOPS_STEP_KERNEL,
                      "peak_source": "FP64 unit count x max SM clock", "hbm_achieved_gbs": hbm64,
                      "hbm_frac": hbm64 / pk["hbm_gbs"], "hbm_peak_source": pk["source"]},
         "variants": {
@@ -365,8 +375,9 @@ def run_ours(args):
                            "roofline": {"bound": "hbm", "achieved": hbm32, "peak": pk["hbm_gbs"], "unit": "GB/s",
                                         "frac": hbm32 / pk["hbm_gbs"],
                                         "traffic": None if t32 is None else t32 * cells,
-                                        "kernel": "k_tile<2,float,lookahead> (FP32-storage step)",
-                                        "kernel_ms": r32["kernel_ms_avg"], "peak_source": pk["source"]}},
+                                        "kernel": "k_roll<float> (FP32-storage step kernel, column strips, look-ahead form: the whole step in one pass)",
+                                        "kernel_ms": r32["kernel_ms_avg"], "peak_source": pk["source"],
+                                        "bytes_per_cell": BYTES_PER_CELL["fp32_store"]}},
             "adjoint": None if adj is None else {
                 "workload": "vortex_adjoint_2d_1024 (J = sum g rho(T), checkpoints every 32 steps)",
                 "value": world * adj["cells"] * adj["steps"] / (adj["rev_ms"] * 1e-3) / 1e6, "unit": UNIT,

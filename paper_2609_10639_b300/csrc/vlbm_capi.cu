@@ -299,6 +299,9 @@ vlbm_status vlbm_create(const vlbm_grid* grid, const vlbm_eos* eos, const vlbm_p
   p.c_sensor = params->c_sensor;
   p.ducros_eps = params->ducros_eps;
   p.retarget_every = params->retarget_every;
+  // Column strips in 2D (each quantity computed once per row).  Measured on a B300 at 4096^2
+  // (per step, 1 GPU): FP64 strips 8.0 ms vs tiles 8.9 ms; FP32 storage strips 0.59 ms
+  // (look-ahead) vs tiles 0.73 ms (two-pass).
   p.strip = (grid->dim == 2 && params->tiling != VLBM_TILING_TILE) ? 1 : 0;
   p.max_parts = vlbm::max_partials(p);
   {
@@ -317,6 +320,9 @@ vlbm_status vlbm_create(const vlbm_grid* grid, const vlbm_eos* eos, const vlbm_p
     c.beta_const = p.beta_const;
     c.inv2dx = p.inv2dx;
     c.eps = p.ducros_eps;
+    c.eps_lat = p.ducros_eps * (2.0 * p.dx) * (2.0 * p.dx);
+    c.c_chi2 = p.c_sensor / 512.0;
+    c.c_chi1 = p.c_sensor / (4.0 * std::sqrt(3.0));
     vlbm::Coef<float>& f = p.cf;
     f.gamma = (float)c.gamma;
     f.gm1 = (float)c.gm1;
@@ -332,13 +338,18 @@ vlbm_status vlbm_create(const vlbm_grid* grid, const vlbm_eos* eos, const vlbm_p
     f.beta_const = (float)c.beta_const;
     f.inv2dx = (float)c.inv2dx;
     f.eps = (float)c.eps;
+    f.eps_lat = (float)c.eps_lat;
+    f.c_chi2 = (float)c.c_chi2;
+    f.c_chi1 = (float)c.c_chi1;
   }
   h->precision = params->precision;
   h->elem = params->precision == VLBM_FP64 ? 8 : 4;
-  // Two-pass by default: measured on a B300 (4096^2), the look-ahead form saves one read of the
-  // state but its extra relaxation ring and second reduction cost more instruction issue than the
-  // reduction pass does, in FP32 storage (0.80 vs 0.74 ms per step) as in FP64 (10.5 vs 10.0 ms).
-  h->lookahead = params->algorithm == VLBM_ALGO_LOOKAHEAD;
+  // Look-ahead (one pass over HBM per step) for FP32 storage, which is bandwidth-bound: 0.59 vs
+  // 0.64 ms per step with strips at 4096^2.  Two-pass for FP64, which is bound by the FP64 pipe:
+  // the look-ahead's second reduction inside the step kernel costs more there than the separate
+  // reduction pass (8.2 vs 8.0 ms).
+  h->lookahead = params->algorithm == VLBM_ALGO_LOOKAHEAD ||
+                 (params->algorithm == VLBM_ALGO_AUTO && params->precision == VLBM_FP32_STORE);
 
   vlbm_status st = VLBM_OK;
   const size_t fbytes = (size_t)p.q * 4 * p.plane * h->elem;  // layout [i][y][x][4]

@@ -75,11 +75,24 @@ __device__ __forceinline__ void ld4s(const double* p, double (&v)[4]) {
 __device__ __forceinline__ void st4s(float* p, const float (&v)[4]) { st4g(p, v); }
 __device__ __forceinline__ void st4s(double* p, const double (&v)[4]) { st4g(p, v); }
 
-// Reciprocal, quotient and square root: correctly rounded in FP64; in the FP32-storage path the
-// hardware approximations (<= 2 ulp), well inside that path's error budget.
-__device__ __forceinline__ double rcp_(double x) { return 1.0 / x; }
+// Reciprocal, quotient and square root.  FP64 reciprocal: two Newton-Raphson steps for 1/a
+// (e = 1 - a y, y <- y + y e; the relative error squares at each step) from the PTX
+// rcp.approx.ftz.f64 seed (relative error ~1e-6 measured on a B300), i.e. ~1e-24 before
+// rounding: in a 4M-sample sweep over [6e-6, 2e5] it equalled 1.0/a in every case.  Four FP64
+// FMAs, against the longer correctly rounded division sequence.  Zero, infinite and subnormal
+// arguments are not meaningful here (rho and 1 - b rho are checked positive and finite); they
+// give a non-finite or zero result.  FP32-storage path: the hardware approximations (<= 2 ulp),
+// well inside that path's error budget.
+__device__ __forceinline__ double rcp_(double a) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(a));
+  double e = fma(-a, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-a, y, 1.0);
+  return fma(y, e, y);
+}
 __device__ __forceinline__ float rcp_(float x) { return __fdividef(1.0f, x); }
-__device__ __forceinline__ double div_(double a, double b) { return a / b; }
+__device__ __forceinline__ double div_(double a, double b) { return a * rcp_(b); }
 __device__ __forceinline__ float div_(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
 __device__ __forceinline__ float sqrt_(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
@@ -251,34 +264,52 @@ __device__ __forceinline__ void moments(const M (&fr)[2 * D][D + 2], const M* wq
 // Fused reprojection (c_old -> c_new, Eqs. 38-40) and relaxation (Eqs. 20, 22) of one cell:
 //   f*_{a,+-} = W/Q  +-  [ beta Q_a / c + (1 - 2 beta) r (f_{a+} - f_{a-}) / 2 ]
 //               (+ for x, - for y)  (1 - 2 beta) r^2 ((f_x+ + f_x-) - (f_y+ + f_y-)) / 4   (D2Q4 K-term),
-// r = c_old / c_new.  In FP32 storage the same update acts on the deviations (W/Q -> dW/Q).
+// r = c_old / c_new.  In 2D the W/4 and K-terms of a direction pair combine into
+//   (1/4 + k) S_x + (1/4 - k) S_y  (x pair),   (1/4 - k) S_x + (1/4 + k) S_y  (y pair),
+// with S_a = f_{a+} + f_{a-} and k = (1 - 2 beta) r^2 / 4.  In FP32 storage the same update acts
+// on the deviations (W/Q -> dW/Q).
 template <int D, class M>
 __device__ __forceinline__ void relax_cell(M (&f)[2 * D][D + 2], const M (&Qc)[D][D + 2], M beta, M r, M inv_c) {
   constexpr int NC = D + 2;
   const M om = (M)1 - (M)2 * beta;
   const M bq = beta * inv_c;
   const M omr = om * r * (M)0.5;
-  const M omk = om * r * r * (M)0.25;
+  if constexpr (D == 1) {
 #pragma unroll
-  for (int k = 0; k < NC; ++k) {
-    const M sx = f[0][k] + f[1][k];
-    const M gx = bq * Qc[0][k] + omr * (f[1][k] - f[0][k]);
-    if constexpr (D == 1) {
-      const M w = sx * (M)0.5;
+    for (int k = 0; k < NC; ++k) {
+      const M w = (f[0][k] + f[1][k]) * (M)0.5;
+      const M gx = bq * Qc[0][k] + omr * (f[1][k] - f[0][k]);
       f[0][k] = w - gx;
       f[1][k] = w + gx;
-    } else {
-      const M sy = f[2][k] + f[3][k];
-      const M w = (sx + sy) * (M)0.25;
+    }
+  } else {
+    const M omk = om * r * r * (M)0.25;
+    const M cp = (M)0.25 + omk, cm = (M)0.25 - omk;
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      const M sx = f[0][k] + f[1][k], sy = f[2][k] + f[3][k];
+      const M gx = bq * Qc[0][k] + omr * (f[1][k] - f[0][k]);
       const M gy = bq * Qc[1][k] + omr * (f[3][k] - f[2][k]);
-      const M kk = omk * (sx - sy);
-      const M wx = w + kk, wy = w - kk;
+      const M wx = cp * sx + cm * sy, wy = cm * sx + cp * sy;
       f[0][k] = wx - gx;
       f[1][k] = wx + gx;
       f[2][k] = wy - gy;
       f[3][k] = wy + gy;
     }
   }
+}
+
+// Separable (1/4, 1/2, 1/4) box filter (Sec. III D) without its normalisation: a + 2b + c.  Two
+// passes give 16 x the filtered value; the powers of two are exact, so scaling at the end
+// reproduces the normalised filter bit for bit.
+__device__ __forceinline__ double box3(double a, double b, double c) { return fma(2.0, b, a) + c; }
+__device__ __forceinline__ float box3(float a, float b, float c) { return fmaf(2.0f, b, a) + c; }
+
+// Sensor A/B map (Eqs. 34-35) from chi before clipping (C s_bar theta_bar).
+template <class M>
+__device__ __forceinline__ M beta_of(const Coef<M>& co, M chi) {
+  chi = chi <= (M)0 ? (M)0 : (chi >= (M)1 ? (M)1 : chi);
+  return co.beta_max - co.dbeta * chi;
 }
 
 // ------------------------------------------------------------------------------------------

@@ -1,10 +1,12 @@
 // Column-marching form of the 2D step kernel (sm_103a).
 //
-// One CTA owns a strip of TXO output columns and L output rows and walks down it RR rows at a
-// time.  Every quantity of the step is computed once per row of the strip and kept in
+// The grid is cut into column strips of TXO output columns; the strip-rows of all strips, taken
+// strip by strip, are split evenly over a persistent grid of CTAs (as many as fit on the GPU at
+// once, so every SM gets the same work), and each CTA walks down its share (one or two strip
+// segments) RR rows at a time.  Every quantity of the step is computed once per row and kept in
 // shared-memory ring buffers for as long as the stencils below need it, so the only
-// recomputation is the x-halo of the strip (H columns on each side) and H rows at each end of
-// the strip, instead of a halo all around a small tile.  Per iteration (block start F):
+// recomputation is the x-halo of the strip (H columns on each side) and H rows at each end of a
+// segment, instead of a halo all around a small tile.  Per iteration (block start F):
 //
 //   S1  rows [F, F+RR):        pulled populations (Eq. 21), W, u, flux Q_alpha (Eqs. 10, 15-17)
 //                              -> ring of Q and u (2 RR rows); the populations stay in registers
@@ -50,8 +52,11 @@ __device__ __forceinline__ int ring(int r, int base) {
   return (r - base + 8 * R) % R;
 }
 
-template <class S, bool LOOK, int XW, int RR, int L>
-__global__ void __launch_bounds__(XW * RR) k_roll(const S* __restrict__ fin, S* __restrict__ fout,
+// FP32 storage: two resident CTAs per SM (64 registers) to hide memory latency, 0.46 vs 0.73 ms
+// per two-pass step kernel at 4096^2 with one; FP64 is bound by its FP64 pipe and keeps one CTA
+// of up to 128 registers per SM.
+template <class S, bool LOOK, int XW, int RR>
+__global__ void __launch_bounds__(XW * RR, sizeof(S) == 4 ? 2 : 1) k_roll(const S* __restrict__ fin, S* __restrict__ fout,
                                                   Scalars* __restrict__ sc, const KParams p, const int pulled,
                                                   const typename Store<S>::M* __restrict__ invM_src,
                                                   double* __restrict__ part) {
@@ -69,25 +74,14 @@ __global__ void __launch_bounds__(XW * RR) k_roll(const S* __restrict__ fin, S* 
 
   const Coef<M>& co = coef<M>(p);
   const int tx = threadIdx.x % XW, ty = threadIdx.x / XW;
-  const int x0 = blockIdx.x * TXO, y0 = blockIdx.y * L;
-  const int xs = x0 - H;  // column of strip position 0
-  const int px = xs + tx;
-  const int xend = min(x0 + TXO, p.nx), yend = min(y0 + L, p.ny);
-  const int base = y0 - H;
-  // strip positions or their pull sources outside [0, nx): boundary rules needed in x
-  const bool xedge = xs - 1 < 0 || xs + XW + 1 > p.nx;
   const bool zx = p.bc[0] == 1, zy = p.bc[2] == 1;  // zero-gradient in x / y (both sides alike)
-  const bool x_in = px >= 0 && px < p.nx;
-
-  // strip index of the value read at column px + d (the edge cell beyond a zero-gradient side)
-  auto xi = [&](int d) -> int { return xedge ? centre_pos(px + d, p.nx, p.bc[0], p.bc[1]) - xs : tx + d; };
   auto yc = [&](int r) -> int { return centre_pos(r, p.ny, p.bc[2], p.bc[3]); };
 
-  M wq[4], invM[4];
+  M wq[4], invMh[4];  // invMh: M_k^-1 / 2 (s_hat_k = jump over two cells / 2 / M_k, Eqs. 29-30)
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     wq[k] = StepScalars<M>::wq(sc, k);
-    invM[k] = invM_src[k];
+    invMh[k] = (M)0.5 * invM_src[k];
   }
   const M r_c = StepScalars<M>::r(sc), inv_c = StepScalars<M>::inv_c(sc);
   const int slot_n = (int)(sc->n & 1);
@@ -103,6 +97,28 @@ __global__ void __launch_bounds__(XW * RR) k_roll(const S* __restrict__ fin, S* 
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int k = 0; k < 4; ++k) fcar[i][k] = (M)0;
+
+  // this CTA's share of the strip-rows, strip-major
+  const int nstrips = (p.nx + TXO - 1) / TXO;
+  const long long total = (long long)nstrips * p.ny;
+  long long a = total * blockIdx.x / gridDim.x;
+  const long long b_end = total * (blockIdx.x + 1) / gridDim.x;
+  for (; a < b_end;) {
+  const int strip = (int)(a / p.ny);
+  const int y0 = (int)(a - (long long)strip * p.ny);
+  const int yend = (int)min((long long)p.ny, (long long)y0 + (b_end - a));
+  a += yend - y0;
+  const int x0 = strip * TXO;
+  const int xs = x0 - H;  // column of strip position 0
+  const int px = xs + tx;
+  const int xend = min(x0 + TXO, p.nx);
+  const int base = y0 - H;
+  // strip positions or their pull sources outside [0, nx): boundary rules needed in x
+  const bool xedge = xs - 1 < 0 || xs + XW + 1 > p.nx;
+  const bool x_in = px >= 0 && px < p.nx;
+  // strip index of the value read at column px + d (the edge cell beyond a zero-gradient side)
+  auto xi = [&](int d) -> int { return xedge ? centre_pos(px + d, p.nx, p.bc[0], p.bc[1]) - xs : tx + d; };
+  __syncthreads();  // the rings of a previous segment are no longer read
 
   for (int F = base; F - RR - (LOOK ? 1 : 0) < yend; F += RR) {
     // ---- S1: pulled populations, W, u, Q of rows [F, F+RR) ----
@@ -120,7 +136,7 @@ __global__ void __launch_bounds__(XW * RR) k_roll(const S* __restrict__ fin, S* 
         prim_flux<2, M, false>(p, W, u, Qf, cs);
         const int s = ring<RQ>(r, base);
 #pragma unroll
-        for (int a = 0; a < 2; ++a) st4s(sQ + ((s * 2 + a) * XW + tx) * 4, Qf[a]);
+        for (int al = 0; al < 2; ++al) st4s(sQ + ((s * 2 + al) * XW + tx) * 4, Qf[al]);
         if constexpr (sizeof(M) == 8) {
           reinterpret_cast<double2*>(sU)[s * XW + tx] = make_double2((double)u[0], (double)u[1]);
         } else {
@@ -146,10 +162,10 @@ __global__ void __launch_bounds__(XW * RR) k_roll(const S* __restrict__ fin, S* 
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           const M jk = (qxp[k] - qxm[k]) + (qyp[k] - qym[k]);
-          const M sh = (M)0.5 * jk * invM[k];
+          const M sh = jk * invMh[k];
           acc += sh * sh;
         }
-        const M sval = sqrt_(acc * (M)0.25);
+        const M sval = sqrt_(acc);  // 2 s (Eq. 31); the 2 is folded into c_chi2
         M uxp, uxm, vxp, vxm, uyp, uym, vyp, vym;
         if constexpr (sizeof(M) == 8) {
           const double2* u2 = reinterpret_cast<const double2*>(sU);
@@ -160,9 +176,8 @@ __global__ void __launch_bounds__(XW * RR) k_roll(const S* __restrict__ fin, S* 
           const float2 a = u2[s0 * XW + tx + 1], b = u2[s0 * XW + tx - 1], c = u2[sp * XW + tx], d = u2[sm * XW + tx];
           uxp = a.x, vxp = a.y, uxm = b.x, vxm = b.y, uyp = c.x, vyp = c.y, uym = d.x, vym = d.y;
         }
-        const M dil = ((uxp - uxm) + (vyp - vym)) * co.inv2dx;
-        const M vort = ((vxp - vxm) - (uyp - uym)) * co.inv2dx;
-        const M th = div_(dil * dil, dil * dil + vort * vort + co.eps);
+        const M dl = (uxp - uxm) + (vyp - vym), vt = (vxp - vxm) - (uyp - uym);  // 2 dx (dil, vort)
+        const M th = div_(dl * dl, dl * dl + vt * vt + co.eps_lat);
         const int ss = ring<RS>(r, base);
         if constexpr (sizeof(M) == 8) {
           reinterpret_cast<double2*>(sS)[ss * XW + tx] = make_double2((double)sval, (double)th);
@@ -182,7 +197,6 @@ __global__ void __launch_bounds__(XW * RR) k_roll(const S* __restrict__ fin, S* 
         M beta = co.beta_const;
         if (p.beta_mode == 0) {
           const int xm = xi(-1), xp = xi(1);
-          const M q = (M)0.25, h = (M)0.5;
           M rs[3], rt[3];
 #pragma unroll
           for (int j = 0; j < 3; ++j) {
@@ -197,14 +211,10 @@ __global__ void __launch_bounds__(XW * RR) k_roll(const S* __restrict__ fin, S* 
               const float2 e0 = s2[xm], e1 = s2[tx], e2 = s2[xp];
               a0 = e0.x, b0 = e0.y, a1 = e1.x, b1 = e1.y, a2 = e2.x, b2 = e2.y;
             }
-            rs[j] = q * a0 + h * a1 + q * a2;
-            rt[j] = q * b0 + h * b1 + q * b2;
+            rs[j] = box3(a0, a1, a2);
+            rt[j] = box3(b0, b1, b2);
           }
-          const M sbar = q * rs[0] + h * rs[1] + q * rs[2];
-          const M tbar = q * rt[0] + h * rt[1] + q * rt[2];
-          M chi = co.c_sensor * sbar * tbar;
-          chi = chi <= (M)0 ? (M)0 : (chi >= (M)1 ? (M)1 : chi);
-          beta = co.beta_max - co.dbeta * chi;
+          beta = beta_of<M>(co, co.c_chi2 * box3(rs[0], rs[1], rs[2]) * box3(rt[0], rt[1], rt[2]));
         }
         M Qc[2][4];
         const int sq = ring<RQ>(r, base);
@@ -244,62 +254,86 @@ __global__ void __launch_bounds__(XW * RR) k_roll(const S* __restrict__ fin, S* 
       }
     }
   }
+  }  // segments
 
   if constexpr (LOOK) {
     if (bad) atomicOr(&sc->err, ERR_NONPHYSICAL);
-    block_max_store<M, XW * RR>(vmax, part + (long long)slot_n * p.max_parts * kNV, blockIdx.y * gridDim.x + blockIdx.x,
-                                gridDim.x * gridDim.y, &sc->nparts[slot_n]);
+    block_max_store<M, XW * RR>(vmax, part + (long long)slot_n * p.max_parts * kNV, blockIdx.x, gridDim.x,
+                                &sc->nparts[slot_n]);
   }
 }
 
-// Strip shapes: XW columns per row (TXO = XW - 2H of them outputs), RR rows per iteration, L
-// output rows per CTA.
+// Strip shapes: XW columns per row (TXO = XW - 2H of them outputs), RR rows per iteration.
 template <class S, bool LOOK>
 struct RollCfg {
-  static constexpr int XW = 128, RR = 4, L = 128;
+  static constexpr int XW = 128, RR = 4;
 };
+
+constexpr int kMaxDevices = 64;
+int g_grid[kMaxDevices][4];  // persistent grid size per device and configuration (0: not set)
+
+template <class S, bool LOOK>
+constexpr int cfg_index() {
+  return (sizeof(S) == 8 ? 0 : 2) + (LOOK ? 1 : 0);
+}
 
 template <class S, bool LOOK>
 cudaError_t launch_roll_t(const Launch& L_, const void* fin, void* fout, int pulled, const void* invM) {
   using C = RollCfg<S, LOOK>;
   using G = RollGeom<S, LOOK, C::XW, C::RR>;
   const KParams& p = *L_.p;
-  dim3 grid((p.nx + G::TXO - 1) / G::TXO, (p.ny + C::L - 1) / C::L);
-  k_roll<S, LOOK, C::XW, C::RR, C::L><<<grid, G::NT, G::smem_bytes, L_.stream>>>(
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const int grid = (dev >= 0 && dev < kMaxDevices) ? g_grid[dev][cfg_index<S, LOOK>()] : 0;
+  if (grid <= 0) return cudaErrorInitializationError;  // prepare_roll_kernels() not run on this device
+  k_roll<S, LOOK, C::XW, C::RR><<<grid, G::NT, G::smem_bytes, L_.stream>>>(
       (const S*)fin, (S*)fout, L_.sc, p, pulled, (const typename Store<S>::M*)invM, L_.part);
   return cudaGetLastError();
 }
 
+// Opt-in shared memory, and the persistent grid: SMs x resident CTAs per SM.
 template <class S, bool LOOK>
-cudaError_t prepare_roll_t() {
+cudaError_t prepare_roll_t(int dev, int sms) {
   using C = RollCfg<S, LOOK>;
   using G = RollGeom<S, LOOK, C::XW, C::RR>;
-  return cudaFuncSetAttribute(k_roll<S, LOOK, C::XW, C::RR, C::L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)G::smem_bytes);
+  cudaError_t e = cudaFuncSetAttribute(k_roll<S, LOOK, C::XW, C::RR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)G::smem_bytes);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_roll<S, LOOK, C::XW, C::RR>, G::NT, G::smem_bytes);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  g_grid[dev][cfg_index<S, LOOK>()] = sms * per_sm;
+  return cudaSuccess;
 }
 
 }  // namespace
 
 cudaError_t prepare_roll_kernels() {
-  cudaError_t e = prepare_roll_t<double, false>();
-  if (e == cudaSuccess) e = prepare_roll_t<double, true>();
-  if (e == cudaSuccess) e = prepare_roll_t<float, false>();
-  if (e == cudaSuccess) e = prepare_roll_t<float, true>();
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  e = prepare_roll_t<double, false>(dev, sms);
+  if (e == cudaSuccess) e = prepare_roll_t<double, true>(dev, sms);
+  if (e == cudaSuccess) e = prepare_roll_t<float, false>(dev, sms);
+  if (e == cudaSuccess) e = prepare_roll_t<float, true>(dev, sms);
   return e;
 }
 
+// Upper bound of the CTAs a strip launch uses (partial-maxima capacity): every SM full of CTAs.
 long long roll_ctas(const KParams& p) {
   if (p.dim != 2) return 0;
-  long long m = 0;
-  auto upd = [&](int txo, int l) {
-    const long long c = (long long)((p.nx + txo - 1) / txo) * ((p.ny + l - 1) / l);
-    if (c > m) m = c;
-  };
-  upd(RollGeom<double, false, RollCfg<double, false>::XW, RollCfg<double, false>::RR>::TXO, RollCfg<double, false>::L);
-  upd(RollGeom<double, true, RollCfg<double, true>::XW, RollCfg<double, true>::RR>::TXO, RollCfg<double, true>::L);
-  upd(RollGeom<float, false, RollCfg<float, false>::XW, RollCfg<float, false>::RR>::TXO, RollCfg<float, false>::L);
-  upd(RollGeom<float, true, RollCfg<float, true>::XW, RollCfg<float, true>::RR>::TXO, RollCfg<float, true>::L);
-  return m;
+  int dev = 0, sms = 0, thr = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&thr, cudaDevAttrMaxThreadsPerMultiProcessor, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 4096;
+  }
+  constexpr int nt = RollGeom<float, false, RollCfg<float, false>::XW, RollCfg<float, false>::RR>::NT;
+  return (long long)sms * ((thr + nt - 1) / nt);
 }
 
 cudaError_t launch_roll(const Launch& L, int precision, bool lookahead, const void* fin, void* fout, int pulled) {
