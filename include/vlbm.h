@@ -206,8 +206,8 @@ vlbm_status vlbm_adjoint(vlbm_t h, const double* W0, int64_t n_steps, int32_t ch
                          double* dJ_dW0, double* dJ_deos);
 
 /* Device time (ms) of the reverse pass (segment recomputation and adjoint steps) of the last
- * vlbm_adjoint call. */
-vlbm_status vlbm_adjoint_timing(vlbm_t h, double* reverse_ms);
+ * vlbm_adjoint call, and of its segment recomputations alone (*recompute_ms, may be NULL). */
+vlbm_status vlbm_adjoint_timing(vlbm_t h, double* reverse_ms, double* recompute_ms);
 
 /* Number of kernel launches one time step issues (for launch accounting). */
 vlbm_status vlbm_launches_per_step(vlbm_t h, int32_t* launches);

@@ -13,7 +13,7 @@
 //
 // Each backward step runs cell-parallel kernels that exchange per-cell intermediates through a
 // workspace of FP64 fields (the forward quantities of step n are recomputed from f^n first):
-//   k_adj_fields   W, u, Q                    k_adj_argmax(+fold)  M_k, argmax, 1/M_k
+//   k_adj_fields   W, u, Q, per-CTA M_k candidates     k_adj_argmax_fold  M_k, argmax, 1/M_k
 //   k_adj_sensor   s_hat, s, theta, dil, vort
 //   k_adj_local    beta; adjoints of relaxation, equilibrium and reprojection; d/d(s_bar, theta_bar)
 //   k_adj_filter   transposed box filters; d/d(s_hat) -> d/dj; dM partial sums (+fold)
@@ -41,7 +41,7 @@ enum {
   F_TH = 19,        // theta
   F_DIL = 20,
   F_VORT = 21,
-  F_BETA = 22,
+  F_BETA = 22,      // (unused slot)
   F_LSB = 23,       // d/d s_bar
   F_LTB = 24,       // d/d theta_bar
   F_LWEQ = 25,      // 4: dJ/dW through the equilibrium
@@ -108,7 +108,7 @@ template <int D>
 __device__ __forceinline__ double flux_vjp(const KParams& p, const double (&W)[D + 2], const double (&lamQ)[D][D + 2],
                                            const double (&lamu)[D], double (&lamW)[D + 2], double (&dP_dprm)[5]) {
   constexpr int NC = D + 2;
-  const double rho = W[0], ir = 1.0 / rho, E = W[NC - 1];
+  const double rho = W[0], ir = rcp_(rho), E = W[NC - 1];
   double u[D], usq = 0.0;
 #pragma unroll
   for (int a = 0; a < D; ++a) {
@@ -182,95 +182,109 @@ __device__ __forceinline__ void load_state(const S* __restrict__ fin, const KPar
 // ------------------------------------------------------------------------------------------
 // kernels (one thread per cell, 256-thread CTAs)
 // ------------------------------------------------------------------------------------------
-template <int D, class S>
-__global__ void __launch_bounds__(kNTA) k_adj_fields(const S* __restrict__ fin, const KParams p, int pulled,
-                                                      const AdjScalars* __restrict__ as, double* __restrict__ F) {
-  constexpr int NC = D + 2;
-  const int cell = blockIdx.x * kNTA + threadIdx.x;
-  if (cell >= p.plane) return;
-  const int cx = cell % p.nx, cy = cell / p.nx;
-  const long long P = p.plane;
-  double fr[2 * D][NC], W[NC], u[D], Qf[D][NC], cs;
-  load_state<D, S>(fin, p, cx, cy, pulled, as->wref, fr);
-  moments<D, double, false>(fr, nullptr, W);
-  prim_flux<D, double, false>(p, W, u, Qf, cs);
-#pragma unroll
-  for (int k = 0; k < NC; ++k) F[(F_W + k) * P + cell] = W[k];
-#pragma unroll
-  for (int a = 0; a < D; ++a) {
-    F[(F_U + a) * P + cell] = u[a];
-#pragma unroll
-    for (int k = 0; k < NC; ++k) F[(F_Q + 4 * a + k) * P + cell] = Qf[a][k];
-  }
-}
-
 // Per-CTA (value, linear index) maxima of |Q_alpha,k| for each k; ties to the lowest index
 // ((alpha NC + k) ny + y) nx + x.
+// The values are non-negative doubles (or +0.0 for "none yet"), compared through their 64-bit
+// patterns on the integer pipe (same order).
 __device__ __forceinline__ bool better(double v, long long i, double bv, long long bi) {
-  return v > bv || (v == bv && i < bi);
+  const unsigned long long a = (unsigned long long)__double_as_longlong(v), b = (unsigned long long)__double_as_longlong(bv);
+  return a > b || (a == b && i < bi);
 }
 
-template <int D>
-__global__ void __launch_bounds__(kNTA) k_adj_argmax(const double* __restrict__ F, const KParams p, double* __restrict__ pv,
-                                                      long long* __restrict__ pi) {
-  constexpr int NC = D + 2;
-  __shared__ double sv[kNTA][NC];
-  __shared__ long long si[kNTA][NC];
-  double bv[NC];
-  long long bi[NC];
-#pragma unroll
-  for (int k = 0; k < NC; ++k) {
-    bv[k] = -1.0;
-    bi[k] = 0x7fffffffffffffffll;
-  }
-  const long long P = p.plane;
-  for (long long cell = (long long)blockIdx.x * kNTA + threadIdx.x; cell < P; cell += (long long)gridDim.x * kNTA)
-#pragma unroll
-    for (int a = 0; a < D; ++a)
-#pragma unroll
-      for (int k = 0; k < NC; ++k) {
-        const double v = fabs(F[(F_Q + 4 * a + k) * P + cell]);
-        const long long idx = (long long)(a * NC + k) * P + cell;
-        if (better(v, idx, bv[k], bi[k])) {
-          bv[k] = v;
-          bi[k] = idx;
-        }
-      }
-#pragma unroll
-  for (int k = 0; k < NC; ++k) {
-    sv[threadIdx.x][k] = bv[k];
-    si[threadIdx.x][k] = bi[k];
-  }
+// Smem tree reduction of per-thread (value, index) candidates over the CTA (kNTA threads) into
+// thread 0's slots.
+__device__ __forceinline__ void argmax_block(double (&sv)[kNTA][4], long long (&si)[kNTA][4], int nc) {
   __syncthreads();
   for (int s = kNTA / 2; s > 0; s >>= 1) {
     if ((int)threadIdx.x < s)
-#pragma unroll
-      for (int k = 0; k < NC; ++k)
+      for (int k = 0; k < nc; ++k)
         if (better(sv[threadIdx.x + s][k], si[threadIdx.x + s][k], sv[threadIdx.x][k], si[threadIdx.x][k])) {
           sv[threadIdx.x][k] = sv[threadIdx.x + s][k];
           si[threadIdx.x][k] = si[threadIdx.x + s][k];
         }
     __syncthreads();
   }
+}
+
+// W, u, Q of the forward state of the step, and the CTA's candidates for M_k (Eq. 30).
+template <int D, class S>
+__global__ void __launch_bounds__(kNTA) k_adj_fields(const S* __restrict__ fin, const KParams p, int pulled,
+                                                      const AdjScalars* __restrict__ as, double* __restrict__ F,
+                                                      double* __restrict__ pv, long long* __restrict__ pi) {
+  constexpr int NC = D + 2;
+  __shared__ double sv[kNTA][4];
+  __shared__ long long si[kNTA][4];
+  const int cell = blockIdx.x * kNTA + threadIdx.x;
+  const long long P = p.plane;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    sv[threadIdx.x][k] = 0.0;
+    si[threadIdx.x][k] = 0x7fffffffffffffffll;
+  }
+  if (cell < p.plane) {
+    const int cx = cell % p.nx, cy = cell / p.nx;
+    double fr[2 * D][NC], W[NC], u[D], Qf[D][NC], cs;
+    load_state<D, S>(fin, p, cx, cy, pulled, as->wref, fr);
+    moments<D, double, false>(fr, nullptr, W);
+    prim_flux<D, double, false>(p, W, u, Qf, cs);
+#pragma unroll
+    for (int k = 0; k < NC; ++k) F[(F_W + k) * P + cell] = W[k];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      F[(F_U + a) * P + cell] = u[a];
+#pragma unroll
+      for (int k = 0; k < NC; ++k) F[(F_Q + 4 * a + k) * P + cell] = Qf[a][k];
+    }
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      // |Q| compared as 64-bit patterns (same order for non-negative doubles; integer pipe);
+      // increasing alpha is increasing index, so a strict > keeps the first
+      unsigned long long best = 0;
+      int ba = -1;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        const unsigned long long v = (unsigned long long)__double_as_longlong(Qf[a][k]) & 0x7fffffffffffffffull;
+        if (ba < 0 || v > best) {
+          best = v;
+          ba = a;
+        }
+      }
+      sv[threadIdx.x][k] = __longlong_as_double((long long)best);
+      si[threadIdx.x][k] = (long long)(ba * NC + k) * P + cell;
+    }
+  }
+  argmax_block(sv, si, NC);
   if ((int)threadIdx.x < NC) {
     pv[blockIdx.x * 4 + threadIdx.x] = sv[0][threadIdx.x];
     pi[blockIdx.x * 4 + threadIdx.x] = si[0][threadIdx.x];
   }
 }
 
-__global__ void k_adj_argmax_fold(const double* __restrict__ pv, const long long* __restrict__ pi, int nparts, int nc,
-                                  AdjScalars* as) {
-  for (int k = 0; k < nc; ++k) {
-    double bv = -1.0;
-    long long bi = 0x7fffffffffffffffll;
-    for (int c = 0; c < nparts; ++c)
-      if (better(pv[c * 4 + k], pi[c * 4 + k], bv, bi)) {
-        bv = pv[c * 4 + k];
-        bi = pi[c * 4 + k];
+// Fold of the per-CTA candidates (one CTA): M_k, 1/M_k and the argmax of each k.
+__global__ void __launch_bounds__(kNTA) k_adj_argmax_fold(const double* __restrict__ pv, const long long* __restrict__ pi,
+                                                           int nparts, int nc, long long plane, AdjScalars* as) {
+  __shared__ double sv[kNTA][4];
+  __shared__ long long si[kNTA][4];
+  for (int k = 0; k < 4; ++k) {
+    sv[threadIdx.x][k] = 0.0;
+    si[threadIdx.x][k] = 0x7fffffffffffffffll;
+  }
+  for (int c = threadIdx.x; c < nparts; c += kNTA)
+    for (int k = 0; k < nc; ++k)
+      if (better(pv[c * 4 + k], pi[c * 4 + k], sv[threadIdx.x][k], si[threadIdx.x][k])) {
+        sv[threadIdx.x][k] = pv[c * 4 + k];
+        si[threadIdx.x][k] = pi[c * 4 + k];
       }
+  argmax_block(sv, si, nc);
+  if ((int)threadIdx.x < nc) {
+    const int k = threadIdx.x;
+    const double bv = sv[0][k];
     as->M[k] = bv;
     as->invM[k] = bv > 0.0 ? 1.0 / bv : 0.0;
-    as->amax[k] = bi;
+    const long long idx = si[0][k];
+    as->amax[k] = idx;
+    as->amax_cell[k] = (int)(idx % plane);
+    as->amax_alpha[k] = (int)((idx / plane) / nc);
   }
 }
 
@@ -317,6 +331,21 @@ __device__ __forceinline__ double sensor_at(const KParams& p, const double* __re
   const long long P = p.plane;
   const double* s = F + F_S * P;
   const double* th = F + F_TH * P;
+  if (D == 2 && x >= 1 && x < p.nx - 1 && y >= 1 && y < p.ny - 1) {  // interior: plain neighbours
+    const int c = y * p.nx + x;
+    double rs[3], rt[3];  // unnormalised (1, 2, 1) sums: the 1/16 is exact
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const int c0 = c + (j - 1) * p.nx;
+      rs[j] = fma(2.0, s[c0], s[c0 - 1]) + s[c0 + 1];
+      rt[j] = fma(2.0, th[c0], th[c0 - 1]) + th[c0 + 1];
+    }
+    sbar = 0.0625 * (fma(2.0, rs[1], rs[0]) + rs[2]);
+    tbar = 0.0625 * (fma(2.0, rt[1], rt[0]) + rt[2]);
+    chi_raw = p.c_sensor * sbar * tbar;
+    const double chi = chi_raw <= 0.0 ? 0.0 : (chi_raw >= 1.0 ? 1.0 : chi_raw);
+    return p.beta_max - (p.beta_max - p.beta_min) * chi;
+  }
   const int xm = nb_index(x - 1, p.nx, p.bc[0], p.bc[1]), xp = nb_index(x + 1, p.nx, p.bc[0], p.bc[1]);
   if constexpr (D == 1) {
     sbar = 0.25 * s[xm] + 0.5 * s[x] + 0.25 * s[xp];
@@ -353,11 +382,19 @@ __global__ void __launch_bounds__(kNTA) k_adj_local(const S* __restrict__ fin, c
   double chi_raw = 0.0, sbar = 0.0, tbar = 1.0, beta;
   if (p.beta_mode == 0) beta = sensor_at<D>(p, F, x, y, chi_raw, sbar, tbar);
   else beta = p.beta_const;
-  F[F_BETA * P + cell] = beta;
   // adjoint of the streaming: lam*_i(x) = sum over y with nb(y - sigma_i) = x of lam_i(y)
   double ls[Q][NC];
+  const bool inner = x >= 1 && x < p.nx - 1 && (D == 1 || (y >= 1 && y < p.ny - 1));
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
+    if (inner) {  // interior: lam*_i(x) = lam_i(x + sigma_i)
+      double v[4];
+      const int src = cell + ((i & 1) ? 1 : -1) * (i < 2 ? 1 : p.nx);
+      ld4g(lam_in + (i * plane + src) * 4, v);
+#pragma unroll
+      for (int k = 0; k < NC; ++k) ls[i][k] = v[k];
+      continue;
+    }
     const int sgn = (i & 1) ? 1 : -1;
     const bool ax = i < 2;
     const int n = ax ? p.nx : p.ny;
@@ -390,29 +427,47 @@ __global__ void __launch_bounds__(kNTA) k_adj_local(const S* __restrict__ fin, c
   for (int a = 0; a < D; ++a)
 #pragma unroll
     for (int k = 0; k < NC; ++k) Qc[a][k] = F[(F_Q + 4 * a + k) * P + cell];
+  // f*_i = 2 beta f^eq_i + (1 - 2 beta) (R f)_i with R the (symmetric) reprojection:
+  //   dJ/df = (1 - 2 beta) R lam*,  dJ/dbeta = 2 sum_i lam*_i f^eq_i - 2 sum_i (R lam*)_i f_i,
+  // and sum_i lam*_i f^eq_i = W/(2D) sum_i lam*_i + 1/(2c) sum_a Q_a (lam*_a+ - lam*_a-).
   double lam_beta = 0.0;
+  const double omb = 1.0 - 2.0 * beta;
+  const double hr = 0.5 * r, qr2 = 0.25 * r * r, hic = 0.5 * inv_c, bic = beta * inv_c, bd = beta / D;
   double out[Q][NC];
 #pragma unroll
   for (int k = 0; k < NC; ++k) {
-    double fk[Q], fp[Q], lk[Q], lr[Q];
-#pragma unroll
-    for (int i = 0; i < Q; ++i) fk[i] = fr[i][k];
-    reproject_k<D>(fk, r, fp);
+    // g = R lam* from the pair sums and differences (which the equilibrium terms reuse)
+    double g[Q], d[D], sum, qd;
+    if constexpr (D == 1) {
+      d[0] = ls[1][k] - ls[0][k];
+      sum = ls[0][k] + ls[1][k];
+      const double w = 0.5 * sum, gx = hr * d[0];
+      g[0] = w - gx;
+      g[1] = w + gx;
+      qd = Qc[0][k] * d[0];
+    } else {
+      const double sx = ls[0][k] + ls[1][k], sy = ls[2][k] + ls[3][k];
+      d[0] = ls[1][k] - ls[0][k];
+      d[1] = ls[3][k] - ls[2][k];
+      sum = sx + sy;
+      const double w = 0.25 * sum, kk = qr2 * (sx - sy), gx = hr * d[0], gy = hr * d[1];
+      const double wx = w + kk, wy = w - kk;
+      g[0] = wx - gx;
+      g[1] = wx + gx;
+      g[2] = wy - gy;
+      g[3] = wy + gy;
+      qd = fma(Qc[0][k], d[0], Qc[1][k] * d[1]);
+    }
+    double gf = 0.0;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      const double feq = W[k] / (2.0 * D) + ((i & 1) ? 1.0 : -1.0) * Qc[i >> 1][k] * 0.5 * inv_c;
-      lam_beta += ls[i][k] * 2.0 * (feq - fp[i]);
-      lk[i] = (1.0 - 2.0 * beta) * ls[i][k];
+      out[i][k] = omb * g[i];
+      gf = fma(g[i], fr[i][k], gf);
     }
-    reproject_k<D>(lk, r, lr);  // transpose of the reprojection (symmetric)
 #pragma unroll
-    for (int i = 0; i < Q; ++i) out[i][k] = lr[i];
-    double sum = 0.0;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) sum += ls[i][k];
-    F[(F_LWEQ + k) * P + cell] = beta / D * sum;  // 2 beta / (2D) sum_i lam*_i
-#pragma unroll
-    for (int a = 0; a < D; ++a) F[(F_LQEQ + 4 * a + k) * P + cell] = beta * inv_c * (ls[2 * a + 1][k] - ls[2 * a][k]);
+    for (int a = 0; a < D; ++a) F[(F_LQEQ + 4 * a + k) * P + cell] = bic * d[a];
+    lam_beta += 2.0 * ((W[k] * (1.0 / (2 * D))) * sum + hic * qd - gf);
+    F[(F_LWEQ + k) * P + cell] = bd * sum;  // 2 beta / (2D) sum_i lam*_i
   }
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
@@ -444,36 +499,58 @@ __global__ void __launch_bounds__(kNTA) k_adj_filter(const KParams p, const AdjS
   if (cell < p.plane) {
     const int x = cell % p.nx, y = cell / p.nx;
     const long long P = p.plane;
-    const Cand cx = candidates(x, p.nx, p.bc[0], p.bc[1]);
-    Cand cy;
-    if constexpr (D == 2) cy = candidates(y, p.ny, p.bc[2], p.bc[3]);
-    else {
-      cy.n = 1;
-      cy.c[0] = 0;
-    }
     double ls = 0.0, lt = 0.0;
-    for (int a = 0; a < cx.n; ++a) {
-      const double wx = filt_w(cx.c[a], x, p.nx, p.bc[0], p.bc[1]);
-      for (int b = 0; b < cy.n; ++b) {
-        const double wy = D == 2 ? filt_w(cy.c[b], y, p.ny, p.bc[2], p.bc[3]) : 1.0;
-        const int src = cy.c[b] * p.nx + cx.c[a];
-        ls += wx * wy * F[F_LSB * P + src];
-        if constexpr (D == 2) lt += wx * wy * F[F_LTB * P + src];
+    const bool inner = x >= 1 && x < p.nx - 1 && (D == 1 || (y >= 1 && y < p.ny - 1));
+    if (inner) {  // the (1/4, 1/2, 1/4) filters are symmetric: their transposes are the filters
+      const double* l1 = F + F_LSB * P;
+      if constexpr (D == 1) {
+        ls = 0.25 * (l1[cell - 1] + 2.0 * l1[cell] + l1[cell + 1]);
+      } else {
+        const double* l2 = F + F_LTB * P;
+        const int nx = p.nx;
+        double rs[3], rt[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          const int c0 = cell + (j - 1) * nx;
+          rs[j] = (l1[c0 - 1] + 2.0 * l1[c0]) + l1[c0 + 1];
+          rt[j] = (l2[c0 - 1] + 2.0 * l2[c0]) + l2[c0 + 1];
+        }
+        ls = 0.0625 * ((rs[0] + 2.0 * rs[1]) + rs[2]);
+        lt = 0.0625 * ((rt[0] + 2.0 * rt[1]) + rt[2]);
+      }
+    } else {  // boundary cells: the distinct cells of the stencil after the boundary rule
+      const Cand cx = candidates(x, p.nx, p.bc[0], p.bc[1]);
+      Cand cy;
+      if constexpr (D == 2) cy = candidates(y, p.ny, p.bc[2], p.bc[3]);
+      else {
+        cy.n = 1;
+        cy.c[0] = 0;
+      }
+      for (int a = 0; a < cx.n; ++a) {
+        const double wx = filt_w(cx.c[a], x, p.nx, p.bc[0], p.bc[1]);
+        for (int b = 0; b < cy.n; ++b) {
+          const double wy = D == 2 ? filt_w(cy.c[b], y, p.ny, p.bc[2], p.bc[3]) : 1.0;
+          const int src = cy.c[b] * p.nx + cx.c[a];
+          ls += wx * wy * F[F_LSB * P + src];
+          if constexpr (D == 2) lt += wx * wy * F[F_LTB * P + src];
+        }
       }
     }
     const double s = F[F_S * P + cell];
+    const double ls_s = s > 0.0 ? ls * rcp_(NC * s) : 0.0;  // d s / d s_hat_k = s_hat_k / (NC s)
 #pragma unroll
     for (int k = 0; k < NC; ++k) {
       const double sh = F[(F_SH + k) * P + cell];
-      const double lsh = s > 0.0 ? ls * sh / (NC * s) : 0.0;
+      const double lsh = ls_s * sh;
       F[(F_LJ + k) * P + cell] = lsh * 0.5 * as->invM[k];  // s_hat = (1/2)(dQ sums) / M
       lM[k] = -lsh * sh * as->invM[k];
     }
     if constexpr (D == 2) {
       const double dil = F[F_DIL * P + cell], vort = F[F_VORT * P + cell];
       const double den = dil * dil + vort * vort + p.ducros_eps;
-      F[F_LDIL * P + cell] = lt * 2.0 * dil * (vort * vort + p.ducros_eps) / (den * den);
-      F[F_LVORT * P + cell] = -lt * 2.0 * vort * dil * dil / (den * den);
+      const double l2 = 2.0 * lt * rcp_(den * den);
+      F[F_LDIL * P + cell] = l2 * dil * (vort * vort + p.ducros_eps);
+      F[F_LVORT * P + cell] = -l2 * vort * dil * dil;
     }
   }
 #pragma unroll
@@ -534,7 +611,24 @@ __global__ void __launch_bounds__(kNTA) k_adj_flux(double* __restrict__ lam_out,
 #pragma unroll
       for (int k = 0; k < NC; ++k) lQ[a][k] = F[(F_LQEQ + 4 * a + k) * P + cell];
     }
-    // transposed central differences along each axis (sensor jumps, dilatation, vorticity)
+    // transposed central differences along each axis (sensor jumps, dilatation, vorticity):
+    // v(x) enters the differences centred at x - 1 (+1) and x + 1 (-1)
+    const bool inner = x >= 1 && x < p.nx - 1 && (D == 1 || (y >= 1 && y < p.ny - 1));
+    if (inner) {
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        const int dn = a == 0 ? 1 : p.nx;
+        const int cm = cell - dn, cp = cell + dn;
+#pragma unroll
+        for (int k = 0; k < NC; ++k) lQ[a][k] += F[(F_LJ + k) * P + cm] - F[(F_LJ + k) * P + cp];
+        if constexpr (D == 2) {
+          const double ld = F[F_LDIL * P + cm] - F[F_LDIL * P + cp], lv = F[F_LVORT * P + cm] - F[F_LVORT * P + cp];
+          lu[a] += p.inv2dx * ld;
+          if (a == 0) lu[1] += p.inv2dx * lv;
+          else lu[0] -= p.inv2dx * lv;
+        }
+      }
+    } else {
 #pragma unroll
     for (int a = 0; a < D; ++a) {
       const bool ax = a == 0;
@@ -555,13 +649,12 @@ __global__ void __launch_bounds__(kNTA) k_adj_flux(double* __restrict__ lam_out,
         }
       }
     }
+    }  // generic (boundary) branch
     // derivative of M_k goes to its argmax element
 #pragma unroll
     for (int k = 0; k < NC; ++k) {
-      const long long idx = as->amax[k];
-      const long long a_k = idx / P;  // alpha * NC + k
-      if (idx % P == cell && a_k % NC == k) {
-        const int a = (int)(a_k / NC);
+      if (as->amax_cell[k] == cell) {
+        const int a = as->amax_alpha[k];
         const double q = F[(F_Q + 4 * a + k) * P + cell];
         lQ[a][k] += (q > 0.0 ? 1.0 : (q < 0.0 ? -1.0 : 0.0)) * as->lamM[k];
       }
@@ -700,11 +793,9 @@ static cudaError_t adj_step_t(const AdjLaunch& A, const S* fin, int pulled, cons
                               long long n) {
   const KParams& p = *A.p;
   const unsigned nb = cells_blocks(p);
-  const unsigned ng = nb < 592 ? nb : 592;
   k_adj_set_step<<<1, 1, 0, A.stream>>>(A.as, A.sched, n);
-  k_adj_fields<D, S><<<nb, kNTA, 0, A.stream>>>(fin, p, pulled, A.as, A.F);
-  k_adj_argmax<D><<<ng, kNTA, 0, A.stream>>>(A.F, p, A.pv, A.pi);
-  k_adj_argmax_fold<<<1, 1, 0, A.stream>>>(A.pv, A.pi, ng, p.nc, A.as);
+  k_adj_fields<D, S><<<nb, kNTA, 0, A.stream>>>(fin, p, pulled, A.as, A.F, A.pv, A.pi);
+  k_adj_argmax_fold<<<1, kNTA, 0, A.stream>>>(A.pv, A.pi, nb, p.nc, p.plane, A.as);
   k_adj_sensor<D><<<nb, kNTA, 0, A.stream>>>(p, A.as, A.F);
   k_adj_local<D, S><<<nb, kNTA, 0, A.stream>>>(fin, lam_in, lam_out, p, pulled, A.as, A.F);
   k_adj_filter<D><<<nb, kNTA, 0, A.stream>>>(p, A.as, A.F, A.part);

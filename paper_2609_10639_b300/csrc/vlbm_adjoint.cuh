@@ -9,6 +9,8 @@ namespace vlbm {
 struct AdjScalars {
   double M[4], invM[4];  // M_k = max |Q_alpha,k| of the step and 1/M_k (0 where M_k = 0)
   long long amax[4];     // linear index ((alpha NC + k) ny + y) nx + x of the first maximal element
+  int amax_cell[4];      // its cell y nx + x and direction alpha
+  int amax_alpha[4];
   double lamM[4];        // dJ/dM_k of the step
   double eos[5];         // dJ/d(gamma, a, b, R, cv), accumulated over the steps
   double eos_comp[5];    // compensation terms of that sum
@@ -22,8 +24,8 @@ struct AdjLaunch {
   cudaStream_t stream;
   const double* sched;  // [c0, c_0, ..., c_{N-1}]: link speed of the initial state and of each step
   double* F;            // adj_num_fields() planes of FP64 workspace
-  double* pv;           // per-CTA argmax values [592][4]
-  long long* pi;        // per-CTA argmax indices [592][4]
+  double* pv;           // per-CTA argmax values [CTAs][4]
+  long long* pi;        // per-CTA argmax indices [CTAs][4]
   double* part;         // per-CTA partial sums [adj_part_entries][8]
 };
 

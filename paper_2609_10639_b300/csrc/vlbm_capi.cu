@@ -67,7 +67,7 @@ struct vlbm_s {
     vlbm::AdjScalars* as = nullptr;
     vlbm::AdjScalars* as_host = nullptr;
     Scalars* sc_backup = nullptr;
-    double fwd_ms = 0.0, rev_ms = 0.0;
+    double fwd_ms = 0.0, rev_ms = 0.0, recompute_ms = 0.0;
   } adj;
   bool profile = false;            // bracket step-kernel launches with events
   std::vector<cudaEvent_t> pev;    // event pool, used in pairs
@@ -790,8 +790,8 @@ vlbm_status vlbm_adjoint(vlbm_t h, const double* W0, int64_t n_steps, int32_t ch
     if (cudaMalloc(&A.lam[0], lam_state * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&A.lam[1], lam_state * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&A.F, (size_t)vlbm::adj_num_fields() * p.plane * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&A.pv, 592 * 4 * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&A.pi, 592 * 4 * sizeof(long long)) != cudaSuccess ||
+        cudaMalloc(&A.pv, (size_t)vlbm::adj_part_entries(p) * 4 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&A.pi, (size_t)vlbm::adj_part_entries(p) * 4 * sizeof(long long)) != cudaSuccess ||
         cudaMalloc(&A.part, (size_t)vlbm::adj_part_entries(p) * 8 * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&A.dJ, wsz * sizeof(double)) != cudaSuccess || cudaMalloc(&A.dW0, wsz * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&A.sc_backup, sizeof(Scalars)) != cudaSuccess ||
@@ -832,11 +832,15 @@ vlbm_status vlbm_adjoint(vlbm_t h, const double* W0, int64_t n_steps, int32_t ch
   FL.sched = A.sched;
   int li = (int)(N & 1);  // lambda^N lives in lam[li]
   VLBM_TRY(vlbm::adj_terminal(L, A.dJ, A.lam[li]));
+  const size_t pev_base = h->pev_used;  // event pairs bracketing the recomputations
   for (long long sgi = (long long)nseg - 1; sgi >= 0; --sgi) {
     const long long n0 = sgi * K, n1 = (n0 + K < N) ? n0 + K : N;
     VLBM_TRY(cudaMemcpyAsync(A.seg, A.ckpt + (size_t)sgi * state, state * sizeof(double), cudaMemcpyDeviceToDevice,
                              h->stream));
     if (n1 - n0 > 1) {  // recompute the segment's states with the recorded link speeds (two-pass form)
+      cudaEvent_t ra, rb;
+      VLBM_TRY(profile_pair(h, &ra, &rb));
+      VLBM_TRY(cudaEventRecord(ra, h->stream));
       VLBM_TRY(vlbm::adj_replay_scalars(h->stream, h->sc, n0, A.sched, N + 1));
       for (long long j = 0; j + 1 < n1 - n0; ++j) {
         const int pulled = (n0 + j >= 1) ? 1 : 0;
@@ -846,6 +850,7 @@ vlbm_status vlbm_adjoint(vlbm_t h, const double* W0, int64_t n_steps, int32_t ch
         VLBM_TRY(vlbm::launch_dt(FL));
         VLBM_TRY(vlbm::launch_step(FL, h->precision, false, fin, fout, pulled));
       }
+      VLBM_TRY(cudaEventRecord(rb, h->stream));
     }
     for (long long n = n1 - 1; n >= n0; --n) {
       const int pulled = n >= 1 ? 1 : 0;
@@ -863,15 +868,23 @@ vlbm_status vlbm_adjoint(vlbm_t h, const double* W0, int64_t n_steps, int32_t ch
   // ev0 was re-recorded at the end of the reverse pass: reverse = [ev1, ev0]
   VLBM_TRY(cudaEventElapsedTime(&r_ms, h->ev1, h->ev0));
   A.rev_ms = r_ms;
+  A.recompute_ms = 0.0;
+  for (size_t e = pev_base; e + 1 < h->pev_used; e += 2) {
+    float m = 0.f;
+    VLBM_TRY(cudaEventElapsedTime(&m, h->pev[e], h->pev[e + 1]));
+    A.recompute_ms += m;
+  }
+  h->pev_used = pev_base;
   if (dJ_deos)
     for (int j = 0; j < 5; ++j) dJ_deos[j] = A.as_host->eos[j];
   st = sync_scalars(h);
   return st;
 }
 
-vlbm_status vlbm_adjoint_timing(vlbm_t h, double* reverse_ms) {
+vlbm_status vlbm_adjoint_timing(vlbm_t h, double* reverse_ms, double* recompute_ms) {
   if (!h || !reverse_ms) return VLBM_E_INVAL;
   *reverse_ms = h->adj.rev_ms;
+  if (recompute_ms) *recompute_ms = h->adj.recompute_ms;
   return VLBM_OK;
 }
 

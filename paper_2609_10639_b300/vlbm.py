@@ -70,7 +70,7 @@ def _load():
         "vlbm_launches_per_step": [V, C.POINTER(I32)],
         "vlbm_set_profiling": [V, I32],
         "vlbm_adjoint": [V, V, I64, I32, V, V, D],
-        "vlbm_adjoint_timing": [V, D],
+        "vlbm_adjoint_timing": [V, D, D],
         "vlbm_get_profile": [V, D, C.POINTER(I64)],
         "vlbm_get_totals": [V, D],
         "vlbm_save_state": [V, V, C.c_size_t, C.POINTER(C.c_size_t)],
@@ -243,11 +243,12 @@ class Solver:
                                  deos.ctypes.data_as(C.POINTER(C.c_double))), "vlbm_adjoint")
         return dJ_dW0, deos
 
-    def adjoint_timing(self) -> float:
-        """Device ms of the reverse pass of the last adjoint call."""
-        ms = C.c_double()
-        _check(_lib.vlbm_adjoint_timing(self._h, C.byref(ms)), "vlbm_adjoint_timing")
-        return ms.value
+    def adjoint_timing(self):
+        """Device ms of the reverse pass of the last adjoint call, and of its segment
+        recomputations alone."""
+        ms, rc = C.c_double(), C.c_double()
+        _check(_lib.vlbm_adjoint_timing(self._h, C.byref(ms), C.byref(rc)), "vlbm_adjoint_timing")
+        return ms.value, rc.value
 
     def set_profiling(self, on: bool) -> None:
         _check(_lib.vlbm_set_profiling(self._h, 1 if on else 0), "vlbm_set_profiling")
