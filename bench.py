@@ -36,10 +36,12 @@ UNIT = "MLUPS"
 # (2D: 4 directions x 4 components x 2).
 BYTES_PER_CELL = {"fp64": 256, "fp32_store": 128}
 # Algorithmic FP64 floating-point operations per 2D cell update (ideal gas, shock sensor), FMA
-# counted as 2, divide and square root as 1 each: 214 for the whole step, of which the step
-# kernel of the two-pass form performs 211 (the maxima pass adds c_s and the comparisons).
+# counted as 2, divide and square root as 1 each: 214 for the whole step.  In the two-pass form
+# the maxima pass computes moments, primitives, EOS and flux (and keeps them for the step
+# kernel), so the step kernel performs the sensor, filters, beta and the fused
+# reprojection/relaxation: 178.
 FP64_FLOPS_PER_CELL = 214
-FP64_FLOPS_STEP_KERNEL = 211
+FP64_FLOPS_STEP_KERNEL = 178
 # Algorithmic bytes of one adjoint step including the recomputation of the forward state (FP64):
 # recompute 256 + read the forward state 128 + read lambda 128 + write lambda 128.
 ADJ_BYTES_PER_CELL = 640

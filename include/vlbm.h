@@ -99,7 +99,8 @@ typedef struct {
 /* Creates a solver for the grid, EOS and parameters, bound to `cuda_stream` (a cudaStream_t, or
  * NULL for the legacy default stream).  Allocates the two population buffers (per cell 2D
  * directions x a 4-wide vector of the D+2 components, 8 bytes per value for VLBM_FP64, 4 for
- * VLBM_FP32_STORE) and scratch on the current
+ * VLBM_FP32_STORE; in FP64 with column strips also W, u and Q of the current state, 14 values per
+ * cell, kept from the maxima pass for the step kernel) and scratch on the current
  * device.  Returns VLBM_E_INVAL for nx, ny < 1, more than (2^31 - 1) / (8 D) cells (134,217,727
  * in 2D, e.g. up to 11585^2), a periodic side without
  * its periodic partner, or parameters outside the ranges above; VLBM_E_NOMEM if allocation

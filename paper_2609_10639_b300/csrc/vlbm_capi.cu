@@ -42,6 +42,7 @@ struct vlbm_s {
   double* scratch = nullptr;  // (D+2) * plane doubles + plane + 8 (beta + 1/M)
   size_t scratch_elems = 0;
   double* fscratch = nullptr;  // populations readback (lazily allocated)
+  double* fields = nullptr;    // FP64 strips: W, u, Q kept from the maxima pass (14 planes)
   bool initialised = false;
   bool unpulled = true;        // the current buffer holds equilibrium populations in place
   bool last_step_pulled = true;
@@ -85,6 +86,7 @@ vlbm::Launch launch_of(vlbm_t h, cudaStream_t s) {
   L.hist_dt = h->hist_dt;
   L.hist_c = h->hist_c;
   L.sched = h->sched;
+  L.fields = h->fields;
   return L;
 }
 
@@ -365,6 +367,9 @@ vlbm_status vlbm_create(const vlbm_grid* grid, const vlbm_eos* eos, const vlbm_p
              cudaMalloc(&h->partial, (size_t)h->nblk_sum * 4 * sizeof(double)) != cudaSuccess ||
              cudaMalloc(&h->part, (size_t)2 * p.max_parts * vlbm::kNV * sizeof(double)) != cudaSuccess) {
     st = VLBM_E_NOMEM;
+  } else if (p.strip && h->precision == VLBM_FP64 &&
+             cudaMalloc(&h->fields, (size_t)14 * p.plane * sizeof(double)) != cudaSuccess) {
+    st = VLBM_E_NOMEM;
   } else if (vlbm::prepare_kernels() != cudaSuccess) {
     st = VLBM_E_CUDA;
   }
@@ -399,6 +404,7 @@ vlbm_status vlbm_destroy(vlbm_t h) {
   cudaFree(h->part);
   cudaFree(h->scratch);
   cudaFree(h->fscratch);
+  cudaFree(h->fields);
   cudaFree(h->adj.ckpt);
   cudaFree(h->adj.seg);
   cudaFree(h->adj.lam[0]);

@@ -83,6 +83,9 @@ struct Launch {
   double* hist_dt;
   double* hist_c;
   const double* sched;
+  double* fields = nullptr;  // FP64 two-pass strips: W, u, Q of the current state, 14 planes
+                             // [W0..3, u0, u1, Qx0..3, Qy0..3][y][x], written by the maxima pass
+                             // and read by the step kernel (nullptr: not kept)
 };
 
 // precision: 0 = FP64, 1 = FP32 storage.  lookahead: fused single-kernel step.

@@ -38,9 +38,12 @@ namespace vlbm {
 // ------------------------------------------------------------------------------------------
 // k_reduce: s_max and M_k of the current state (two-pass form; also feeds vlbm_get_beta)
 // ------------------------------------------------------------------------------------------
+// With `fields` (FP64, 2D) the pass also stores W, u and Q of every cell, so that the step
+// kernel reads them instead of recomputing moments, primitives and flux.
 template <int D, class S, int NT>
 __global__ void __launch_bounds__(NT) k_reduce(const S* __restrict__ fin, Scalars* __restrict__ sc, const KParams p,
-                                                const int pulled, double* __restrict__ part, const int in_run) {
+                                                const int pulled, double* __restrict__ part, const int in_run,
+                                                double* __restrict__ fields) {
   using M = typename Store<S>::M;
   using R = Red<M>;
   constexpr int NC = D + 2;
@@ -60,6 +63,18 @@ __global__ void __launch_bounds__(NT) k_reduce(const S* __restrict__ fin, Scalar
     moments<D, M, Store<S>::kOffset>(fr, wq, W);
     bad |= !prim_flux<D, M, true>(p, W, u, Qf, cs);
     cell_maxima<D, M>(u, cs, Qf, v);
+    if constexpr (D == 2 && std::is_same<M, double>::value) {
+      if (fields) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) fields[k * p.plane + cell] = W[k];
+        fields[4 * p.plane + cell] = u[0];
+        fields[5 * p.plane + cell] = u[1];
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+          for (int k = 0; k < 4; ++k) fields[(6 + 4 * a + k) * p.plane + cell] = Qf[a][k];
+      }
+    }
   }
   if (bad) atomicOr(&sc->err, ERR_NONPHYSICAL);
   block_max_store<M, NT>(v, part + (long long)slot * p.max_parts * kNV, blockIdx.x, gridDim.x, &sc->nparts[slot]);
@@ -625,7 +640,8 @@ unsigned blocks_gs(const KParams& p) {
 
 template <int D, class S>
 void launch_reduce_t(const Launch& L, const void* fin, int pulled, int in_run) {
-  k_reduce<D, S, kNT1><<<blocks_gs(*L.p), kNT1, 0, L.stream>>>((const S*)fin, L.sc, *L.p, pulled, L.part, in_run);
+  k_reduce<D, S, kNT1><<<blocks_gs(*L.p), kNT1, 0, L.stream>>>((const S*)fin, L.sc, *L.p, pulled, L.part, in_run,
+                                                                 in_run ? L.fields : nullptr);
 }
 }  // namespace
 
@@ -891,8 +907,8 @@ extern "C" vlbm_status vlbm_beta_noalloc(const vlbm_grid* grid, const vlbm_eos* 
   // The scalar block must start at zero (no error bit, step 0); the partials and 1/M_k are
   // fully written by this call before they are read.
   if (cudaMemsetAsync(sc, 0, sizeof(Scalars), s) != cudaSuccess) return VLBM_E_CUDA;
-  if (p.dim == 1) k_reduce<1, double, kNoallocCtaCells><<<ncta, kNoallocCtaCells, 0, s>>>(f, sc, p, pulled, part, 0);
-  else k_reduce<2, double, kNoallocCtaCells><<<ncta, kNoallocCtaCells, 0, s>>>(f, sc, p, pulled, part, 0);
+  if (p.dim == 1) k_reduce<1, double, kNoallocCtaCells><<<ncta, kNoallocCtaCells, 0, s>>>(f, sc, p, pulled, part, 0, nullptr);
+  else k_reduce<2, double, kNoallocCtaCells><<<ncta, kNoallocCtaCells, 0, s>>>(f, sc, p, pulled, part, 0, nullptr);
   k_beta_prep<<<1, kNTD, 0, s>>>(sc, p, part, invM);
   if (p.dim == 1) {
     constexpr int TX = TileCfg<1>::TX, TY = TileCfg<1>::TY;

@@ -22,6 +22,8 @@
 // Boundary rules as in the tile kernel: positions and rows outside a zero-gradient side hold the
 // edge cell's populations (S1 maps them), and every stencil read of s, theta (S3) and of the
 // relaxed populations (S4) is taken at the edge cell there; periodic sides are unwrapped.
+#include <type_traits>
+
 #include "vlbm.h"
 #include "vlbm_device.cuh"
 #include "vlbm_internal.cuh"
@@ -44,6 +46,7 @@ struct RollGeom {
   static constexpr size_t nS = (size_t)RS * XW * 2;
   static constexpr size_t nF = LOOK ? (size_t)RF * 4 * XW * 4 : 0;
   static constexpr size_t smem_bytes = (nQ + nU + nS + nF) * sizeof(M);
+  static_assert(RR >= 2, "stage S2 of a block reads u/Q one row beyond it");
 };
 
 // Ring slot of row r (rows never lie more than 8 R below the strip's first row `base`).
@@ -52,14 +55,14 @@ __device__ __forceinline__ int ring(int r, int base) {
   return (r - base + 8 * R) % R;
 }
 
-// FP32 storage: two resident CTAs per SM (64 registers) to hide memory latency, 0.46 vs 0.73 ms
-// per two-pass step kernel at 4096^2 with one; FP64 is bound by its FP64 pipe and keeps one CTA
-// of up to 128 registers per SM.
+// FP32 storage: 1024 resident threads per SM (64 registers) to hide memory latency (0.46 vs
+// 0.73 ms per two-pass step kernel at 4096^2 with half of them); FP64 is bound by its FP64 pipe
+// and keeps one CTA of up to 128 registers per SM.
 template <class S, bool LOOK, int XW, int RR>
-__global__ void __launch_bounds__(XW * RR, sizeof(S) == 4 ? 2 : 1) k_roll(const S* __restrict__ fin, S* __restrict__ fout,
+__global__ void __launch_bounds__(XW * RR, sizeof(S) == 4 ? 1024 / (XW * RR) : 1) k_roll(const S* __restrict__ fin, S* __restrict__ fout,
                                                   Scalars* __restrict__ sc, const KParams p, const int pulled,
                                                   const typename Store<S>::M* __restrict__ invM_src,
-                                                  double* __restrict__ part) {
+                                                  double* __restrict__ part, const double* __restrict__ fields) {
   using G = RollGeom<S, LOOK, XW, RR>;
   using M = typename G::M;
   constexpr int H = G::H, TXO = G::TXO, RQ = G::RQ, RS = G::RS, RF = G::RF;
@@ -132,8 +135,26 @@ __global__ void __launch_bounds__(XW * RR, sizeof(S) == 4 ? 2 : 1) k_roll(const 
         const bool inner = !xedge && cy >= 1 && cy < p.ny - 1;
         load_cell<2, S>(fin, p, cx, cy, pulled, inner, fnew);
         M W[4], u[2], Qf[2][4], cs;
-        moments<2, M, OFF>(fnew, wq, W);
-        prim_flux<2, M, false>(p, W, u, Qf, cs);
+        bool have = false;
+        if constexpr (!LOOK && std::is_same<M, double>::value) {
+          if (fields) {  // W, u, Q of this state, stored by the maxima pass
+            const int c = cy * p.nx + cx;
+            const long long P = p.plane;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) W[k] = fields[k * P + c];
+            u[0] = fields[4 * P + c];
+            u[1] = fields[5 * P + c];
+#pragma unroll
+            for (int al = 0; al < 2; ++al)
+#pragma unroll
+              for (int k = 0; k < 4; ++k) Qf[al][k] = fields[(6 + 4 * al + k) * P + c];
+            have = true;
+          }
+        }
+        if (!have) {
+          moments<2, M, OFF>(fnew, wq, W);
+          prim_flux<2, M, false>(p, W, u, Qf, cs);
+        }
         const int s = ring<RQ>(r, base);
 #pragma unroll
         for (int al = 0; al < 2; ++al) st4s(sQ + ((s * 2 + al) * XW + tx) * 4, Qf[al]);
@@ -264,9 +285,12 @@ __global__ void __launch_bounds__(XW * RR, sizeof(S) == 4 ? 2 : 1) k_roll(const 
 }
 
 // Strip shapes: XW columns per row (TXO = XW - 2H of them outputs), RR rows per iteration.
+// FP32 storage: 128 x 2 threads (rings of 4 rows, 56 KB, four CTAs per SM); measured on a B300
+// at 4096^2 the two-pass step kernel takes 0.42 ms this way against 0.46 ms with 128 x 4.
+// FP64: 128 x 4 threads, one CTA per SM.
 template <class S, bool LOOK>
 struct RollCfg {
-  static constexpr int XW = 128, RR = 4;
+  static constexpr int XW = 128, RR = sizeof(S) == 4 ? 2 : 4;
 };
 
 constexpr int kMaxDevices = 64;
@@ -288,7 +312,8 @@ cudaError_t launch_roll_t(const Launch& L_, const void* fin, void* fout, int pul
   const int grid = (dev >= 0 && dev < kMaxDevices) ? g_grid[dev][cfg_index<S, LOOK>()] : 0;
   if (grid <= 0) return cudaErrorInitializationError;  // prepare_roll_kernels() not run on this device
   k_roll<S, LOOK, C::XW, C::RR><<<grid, G::NT, G::smem_bytes, L_.stream>>>(
-      (const S*)fin, (S*)fout, L_.sc, p, pulled, (const typename Store<S>::M*)invM, L_.part);
+      (const S*)fin, (S*)fout, L_.sc, p, pulled, (const typename Store<S>::M*)invM, L_.part,
+      (!LOOK && sizeof(S) == 8) ? L_.fields : nullptr);
   return cudaGetLastError();
 }
 
