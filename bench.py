@@ -35,6 +35,9 @@ UNIT = "MLUPS"
 # Algorithmic bytes per cell update: every population read once and written once
 # (2D: 4 directions x 4 components x 2).
 BYTES_PER_CELL = {"fp64": 256, "fp32_store": 128}
+# The FP64 step kernel of the two-pass form also reads W, u and Q kept by the maxima pass
+# (14 doubles per cell).
+FP64_STEP_KERNEL_BYTES = 256 + 112
 # Algorithmic FP64 floating-point operations per 2D cell update (ideal gas, shock sensor), FMA
 # counted as 2, divide and square root as 1 each: 214 for the whole step.  In the two-pass form
 # the maxima pass computes moments, primitives, EOS and flux (and keeps them for the step
@@ -360,7 +363,7 @@ def run_ours(args):
     k32_s = r32["kernel_ms_avg"] * 1e-3
     fp64_ach = FP64_FLOPS_STEP_KERNEL * cells / k64_s / 1e12
     fp64_peak = fp64_peak_tflops(pk["sm_max_mhz"])
-    hbm64 = BYTES_PER_CELL["fp64"] * cells / k64_s / 1e9
+    hbm64 = FP64_STEP_KERNEL_BYTES * cells / k64_s / 1e9
     hbm32 = BYTES_PER_CELL["fp32_store"] * cells / k32_s / 1e9
     t64 = kernel_traffic("fp64_step")
     t32 = kernel_traffic("fp32_store_step")

@@ -7,10 +7,12 @@
 // each population is read once and written once per step.  The first step after vlbm_init reads
 // the equilibrium populations in place ("unpulled").
 //
-// Step kernel (k_tile): one CTA owns a TX x TY tile and stages, in shared memory, the primitive
-// velocity and the flux Q_alpha(W) of a halo region around it (radius 2, or 3 for the look-ahead
-// form); the shock sensor (Eqs. 28-35) and its separable box filter read that region; the
-// reprojection (Eqs. 38-40) and relaxation (Eqs. 20, 22) are fused into one register update.
+// Step kernels: the 2D default is the column-strip kernel k_roll (vlbm_roll.cu).  This file holds
+// the tile kernel k_tile (1D, beta readback, and 2D on request): one CTA owns a TX x TY tile and
+// stages, in shared memory, the primitive velocity and the flux Q_alpha(W) of a halo region
+// around it (radius 2, or 3 for the look-ahead form); the shock sensor (Eqs. 28-35) and its
+// separable box filter read that region; the reprojection (Eqs. 38-40) and relaxation (Eqs. 20,
+// 22) are fused into one register update.
 // Boundary rules are applied to every stencil access: a region position outside a zero-gradient
 // side takes the values of the edge cell (edge-replicated ghost) and every derived stencil
 // quantity there is evaluated at the edge cell; periodic sides are simply unwrapped.
@@ -18,10 +20,11 @@
 // The two domain-wide maxima a step needs (s_max, Eq. 36; M_k, Eq. 30) are reduced with warp
 // shuffles and a per-CTA combine into per-CTA partials, folded by the one-CTA link-speed kernel
 // (no atomics, deterministic).  Two forms:
-//   two-pass:   k_reduce (reads the state once more) -> k_dt -> k_tile;
-//   look-ahead: k_dt -> k_tile, where k_tile also relaxes a one-cell ring around its tile,
-//               streams those populations into W^{n+1} of its cells and reduces them for the next
-//               step, so a step moves each population through HBM exactly twice.
+//   two-pass:   k_reduce (reads the state once more; in FP64 with strips it also keeps W, u, Q
+//               for the step kernel) -> k_dt -> step kernel;
+//   look-ahead: k_dt -> step kernel, which also forms W^{n+1} of its cells from the relaxed
+//               populations (k_tile: a one-cell ring around its tile) and reduces them for the
+//               next step, so a step moves each population through HBM exactly twice.
 // k_dt is a one-CTA kernel that folds the partial maxima and turns them into c, dt, r and 1/M_k
 // on the device.
 #include "vlbm.h"
