@@ -399,10 +399,12 @@ def run_ours(args):
                 "recompute_ms": adj["rec_ms"],
                 "reverse_over_forward": adj["rev_ms"] / adj["fwd_ms"],
                 "adjoint_step_over_forward_step": (adj["rev_ms"] - adj["rec_ms"]) / adj["fwd_ms"],
-                "roofline": {"bound": "hbm", "unit": "GB/s", "peak": pk["hbm_gbs"],
-                             "achieved": ADJ_BYTES_PER_CELL * adj["cells"] * adj["steps"] / (adj["rev_ms"] * 1e-3) / 1e9,
-                             "frac": ADJ_BYTES_PER_CELL * adj["cells"] * adj["steps"] / (adj["rev_ms"] * 1e-3) / 1e9 / pk["hbm_gbs"],
-                             "traffic": None, "note": "algorithmic 640 B/cell: recompute 256, state 128, lambda 128 + 128"}},
+                "roofline": {"bound": "alu",
+                             "note": "every adjoint kernel is FP64-pipe bound (ncu: "
+                                     "profiles/adjoint_kernels_vortex_1024.md)",
+                             "hbm_achieved_gbs": ADJ_BYTES_PER_CELL * adj["cells"] * adj["steps"] / (adj["rev_ms"] * 1e-3) / 1e9,
+                             "hbm_frac": ADJ_BYTES_PER_CELL * adj["cells"] * adj["steps"] / (adj["rev_ms"] * 1e-3) / 1e9 / pk["hbm_gbs"],
+                             "hbm_bytes_per_cell": ADJ_BYTES_PER_CELL}},
         },
         "cpu_baseline": cpu,
         "e2e": {"value": e2e64, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},

@@ -320,8 +320,6 @@ vlbm_status vlbm_create(const vlbm_grid* grid, const vlbm_eos* eos, const vlbm_p
     c.beta_max = p.beta_max;
     c.dbeta = p.beta_max - p.beta_min;
     c.beta_const = p.beta_const;
-    c.inv2dx = p.inv2dx;
-    c.eps = p.ducros_eps;
     c.eps_lat = p.ducros_eps * (2.0 * p.dx) * (2.0 * p.dx);
     c.c_chi2 = p.c_sensor / 512.0;
     c.c_chi1 = p.c_sensor / (4.0 * std::sqrt(3.0));
@@ -338,8 +336,6 @@ vlbm_status vlbm_create(const vlbm_grid* grid, const vlbm_eos* eos, const vlbm_p
     f.beta_max = (float)c.beta_max;
     f.dbeta = (float)c.dbeta;
     f.beta_const = (float)c.beta_const;
-    f.inv2dx = (float)c.inv2dx;
-    f.eps = (float)c.eps;
     f.eps_lat = (float)c.eps_lat;
     f.c_chi2 = (float)c.c_chi2;
     f.c_chi1 = (float)c.c_chi1;

@@ -49,10 +49,9 @@ struct Coef {
   M c_chi2, c_chi1;             // chi = c_chi2 S T (2D) or c_chi1 S (1D), S and T the unnormalised
                                 // filter sums of sqrt(sum_k s_hat_k^2) and theta: C / 512, C / (4 sqrt 3)
   M beta_const;                 // constant-beta mode
-  M inv2dx, eps;                // 1/(2 dx), Ducros regulariser              (Eqs. 32-33)
-  M eps_lat;                    // the regulariser in units of unscaled central differences,
-                                // eps (2 dx)^2: theta = D^2 / (D^2 + V^2 + eps_lat) with
-                                // D, V the dilatation and vorticity times 2 dx
+  M eps_lat;                    // Ducros regulariser (Eqs. 32-33) in units of unscaled central
+                                // differences, eps (2 dx)^2: theta = D^2 / (D^2 + V^2 + eps_lat)
+                                // with D, V the dilatation and vorticity times 2 dx
 };
 
 // Constant per-solver parameters, passed to kernels by value.

@@ -899,8 +899,6 @@ extern "C" vlbm_status vlbm_beta_noalloc(const vlbm_grid* grid, const vlbm_eos* 
   c.beta_max = p.beta_max;
   c.dbeta = p.beta_max - p.beta_min;
   c.beta_const = p.beta_const;
-  c.inv2dx = p.inv2dx;
-  c.eps = p.ducros_eps;
   c.eps_lat = p.ducros_eps * (2.0 * p.dx) * (2.0 * p.dx);
   c.c_chi2 = p.c_sensor / 512.0;
   c.c_chi1 = p.c_sensor / (4.0 * sqrt(3.0));

@@ -32,7 +32,7 @@ def _rank(rank, world, port, out):
 @pytest.mark.timeout(120)
 def test_two_gloo_ranks_max_and_aggregate():
     port = 29500 + os.getpid() % 1000
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.spawn(_rank, args=(2, port, out), nprocs=2, join=True)
         res = dict(out)
