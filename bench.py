@@ -321,6 +321,13 @@ def run_only(args):
     from paper_2609_10639_b300 import workloads as wl
 
     world, rank, local = dist_init()
+    if args.only == "adjoint":
+        adj = time_adjoint(args.adjoint_steps, 32, world)
+        if rank == 0:
+            print(json.dumps({"only": "adjoint", **adj, "reverse_over_forward": adj["rev_ms"] / adj["fwd_ms"],
+                              "adjoint_step_over_forward_step": (adj["rev_ms"] - adj["rec_ms"]) / adj["fwd_ms"]}),
+                  flush=True)
+        return
     prob = wl.QUADRANTS_2D.resized(args.grid) if args.grid else wl.QUADRANTS_2D
     W0 = torch.from_numpy(wl.quadrants_2d(prob)).cuda()
     r = time_path(prob, W0, args.only, args.substeps, args.steps, args.warmup, world)
@@ -423,7 +430,8 @@ def main():
     ap.add_argument("--substeps", type=int, default=32)
     ap.add_argument("--adjoint-steps", type=int, default=1000, help="steps of the adjoint measurement (0: skip)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--only", choices=list(BYTES_PER_CELL), help="time one path only (profiling, sweeps)")
+    ap.add_argument("--only", choices=list(BYTES_PER_CELL) + ["adjoint"],
+                    help="time one path only (profiling, sweeps); adjoint: the adjoint measurement alone")
     ap.add_argument("--grid", type=int, default=0, help="with --only: n x n copy of the workload")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -14,6 +14,9 @@
 // Each backward step runs cell-parallel kernels that exchange per-cell intermediates through a
 // workspace of FP64 fields (the forward quantities of step n are recomputed from f^n first):
 //   k_adj_fields   W, u, Q, per-CTA M_k candidates     k_adj_argmax_fold  M_k, argmax, 1/M_k
+//                  (k_adj_argmax_kept: the candidates only, when the forward recomputation kept
+//                  W, u, Q of the state; its step kernel then also kept the sensor quantities,
+//                  and k_adj_sensor does not run)
 //   k_adj_sensor   s_hat, s, theta, dil, vort
 //   k_adj_local    beta; adjoints of relaxation, equilibrium and reprojection; d/d(s_bar, theta_bar)
 //   k_adj_filter   transposed box filters; d/d(s_hat) -> d/dj; dM partial sums (+fold)
@@ -260,6 +263,46 @@ __global__ void __launch_bounds__(kNTA) k_adj_fields(const S* __restrict__ fin, 
   }
 }
 
+// The CTA's candidates for M_k from Q kept by the forward recomputation (same layout as the
+// workspace's first planes).
+template <int D>
+__global__ void __launch_bounds__(kNTA) k_adj_argmax_kept(const double* __restrict__ WQ, const KParams p,
+                                                           double* __restrict__ pv, long long* __restrict__ pi) {
+  constexpr int NC = D + 2;
+  __shared__ double sv[kNTA][4];
+  __shared__ long long si[kNTA][4];
+  const int cell = blockIdx.x * kNTA + threadIdx.x;
+  const long long P = p.plane;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    sv[threadIdx.x][k] = 0.0;
+    si[threadIdx.x][k] = 0x7fffffffffffffffll;
+  }
+  if (cell < p.plane) {
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      unsigned long long best = 0;
+      int ba = -1;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        const unsigned long long v =
+            (unsigned long long)__double_as_longlong(WQ[(F_Q + 4 * a + k) * P + cell]) & 0x7fffffffffffffffull;
+        if (ba < 0 || v > best) {
+          best = v;
+          ba = a;
+        }
+      }
+      sv[threadIdx.x][k] = __longlong_as_double((long long)best);
+      si[threadIdx.x][k] = (long long)(ba * NC + k) * P + cell;
+    }
+  }
+  argmax_block(sv, si, NC);
+  if ((int)threadIdx.x < NC) {
+    pv[blockIdx.x * 4 + threadIdx.x] = sv[0][threadIdx.x];
+    pi[blockIdx.x * 4 + threadIdx.x] = si[0][threadIdx.x];
+  }
+}
+
 // Fold of the per-CTA candidates (one CTA): M_k, 1/M_k and the argmax of each k.
 __global__ void __launch_bounds__(kNTA) k_adj_argmax_fold(const double* __restrict__ pv, const long long* __restrict__ pi,
                                                            int nparts, int nc, long long plane, AdjScalars* as) {
@@ -290,7 +333,7 @@ __global__ void __launch_bounds__(kNTA) k_adj_argmax_fold(const double* __restri
 
 template <int D>
 __global__ void __launch_bounds__(kNTA) k_adj_sensor(const KParams p, const AdjScalars* __restrict__ as,
-                                                      double* __restrict__ F) {
+                                                      double* F, const double* WQ) {
   constexpr int NC = D + 2;
   const int cell = blockIdx.x * kNTA + threadIdx.x;
   if (cell >= p.plane) return;
@@ -305,16 +348,16 @@ __global__ void __launch_bounds__(kNTA) k_adj_sensor(const KParams p, const AdjS
   double acc = 0.0;
 #pragma unroll
   for (int k = 0; k < NC; ++k) {
-    double jk = F[(F_Q + k) * P + xp] - F[(F_Q + k) * P + xm];
-    if constexpr (D == 2) jk += F[(F_Q + 4 + k) * P + yp] - F[(F_Q + 4 + k) * P + ym];
+    double jk = WQ[(F_Q + k) * P + xp] - WQ[(F_Q + k) * P + xm];
+    if constexpr (D == 2) jk += WQ[(F_Q + 4 + k) * P + yp] - WQ[(F_Q + 4 + k) * P + ym];
     const double sh = 0.5 * jk * as->invM[k];
     F[(F_SH + k) * P + cell] = sh;
     acc += sh * sh;
   }
   F[F_S * P + cell] = sqrt(acc * (1.0 / NC));
   if constexpr (D == 2) {
-    const double* ux = F + F_U * P;
-    const double* uy = F + (F_U + 1) * P;
+    const double* ux = WQ + F_U * P;
+    const double* uy = WQ + (F_U + 1) * P;
     const double dil = ((ux[xp] - ux[xm]) + (uy[yp] - uy[ym])) * p.inv2dx;
     const double vort = ((uy[xp] - uy[xm]) - (ux[yp] - ux[ym])) * p.inv2dx;
     F[F_DIL * P + cell] = dil;
@@ -370,7 +413,8 @@ __device__ __forceinline__ double sensor_at(const KParams& p, const double* __re
 template <int D, class S>
 __global__ void __launch_bounds__(kNTA) k_adj_local(const S* __restrict__ fin, const double* __restrict__ lam_in,
                                                      double* __restrict__ lam_out, const KParams p, int pulled,
-                                                     const AdjScalars* __restrict__ as, double* __restrict__ F) {
+                                                     const AdjScalars* __restrict__ as, double* __restrict__ F,
+                                                     const double* __restrict__ WQ) {
   constexpr int NC = D + 2, Q = 2 * D;
   const int cell = blockIdx.x * kNTA + threadIdx.x;
   if (cell >= p.plane) return;
@@ -380,7 +424,7 @@ __global__ void __launch_bounds__(kNTA) k_adj_local(const S* __restrict__ fin, c
   const double r = as->r, inv_c = as->inv_c;
   // beta of the forward step
   double chi_raw = 0.0, sbar = 0.0, tbar = 1.0, beta;
-  if (p.beta_mode == 0) beta = sensor_at<D>(p, F, x, y, chi_raw, sbar, tbar);
+  if (p.beta_mode == 0) beta = sensor_at<D>(p, WQ, x, y, chi_raw, sbar, tbar);
   else beta = p.beta_const;
   // adjoint of the streaming: lam*_i(x) = sum over y with nb(y - sigma_i) = x of lam_i(y)
   double ls[Q][NC];
@@ -422,11 +466,11 @@ __global__ void __launch_bounds__(kNTA) k_adj_local(const S* __restrict__ fin, c
   load_state<D, S>(fin, p, x, y, pulled, as->wref, fr);
   double W[NC], Qc[D][NC];
 #pragma unroll
-  for (int k = 0; k < NC; ++k) W[k] = F[(F_W + k) * P + cell];
+  for (int k = 0; k < NC; ++k) W[k] = WQ[(F_W + k) * P + cell];
 #pragma unroll
   for (int a = 0; a < D; ++a)
 #pragma unroll
-    for (int k = 0; k < NC; ++k) Qc[a][k] = F[(F_Q + 4 * a + k) * P + cell];
+    for (int k = 0; k < NC; ++k) Qc[a][k] = WQ[(F_Q + 4 * a + k) * P + cell];
   // f*_i = 2 beta f^eq_i + (1 - 2 beta) (R f)_i with R the (symmetric) reprojection:
   //   dJ/df = (1 - 2 beta) R lam*,  dJ/dbeta = 2 sum_i lam*_i f^eq_i - 2 sum_i (R lam*)_i f_i,
   // and sum_i lam*_i f^eq_i = W/(2D) sum_i lam*_i + 1/(2c) sum_a Q_a (lam*_a+ - lam*_a-).
@@ -491,7 +535,8 @@ __global__ void __launch_bounds__(kNTA) k_adj_local(const S* __restrict__ fin, c
 // per-CTA partial sums of dJ/dM_k.
 template <int D>
 __global__ void __launch_bounds__(kNTA) k_adj_filter(const KParams p, const AdjScalars* __restrict__ as,
-                                                      double* __restrict__ F, double* __restrict__ part) {
+                                                      double* __restrict__ F, double* __restrict__ part,
+                                                      const double* __restrict__ WQ) {
   constexpr int NC = D + 2;
   __shared__ double red[kNTA][4];
   const int cell = blockIdx.x * kNTA + threadIdx.x;
@@ -536,17 +581,17 @@ __global__ void __launch_bounds__(kNTA) k_adj_filter(const KParams p, const AdjS
         }
       }
     }
-    const double s = F[F_S * P + cell];
+    const double s = WQ[F_S * P + cell];
     const double ls_s = s > 0.0 ? ls * rcp_(NC * s) : 0.0;  // d s / d s_hat_k = s_hat_k / (NC s)
 #pragma unroll
     for (int k = 0; k < NC; ++k) {
-      const double sh = F[(F_SH + k) * P + cell];
+      const double sh = WQ[(F_SH + k) * P + cell];
       const double lsh = ls_s * sh;
       F[(F_LJ + k) * P + cell] = lsh * 0.5 * as->invM[k];  // s_hat = (1/2)(dQ sums) / M
       lM[k] = -lsh * sh * as->invM[k];
     }
     if constexpr (D == 2) {
-      const double dil = F[F_DIL * P + cell], vort = F[F_VORT * P + cell];
+      const double dil = WQ[F_DIL * P + cell], vort = WQ[F_VORT * P + cell];
       const double den = dil * dil + vort * vort + p.ducros_eps;
       const double l2 = 2.0 * lt * rcp_(den * den);
       F[F_LDIL * P + cell] = l2 * dil * (vort * vort + p.ducros_eps);
@@ -595,7 +640,8 @@ __global__ void __launch_bounds__(kNTA) k_adj_fold(const double* __restrict__ pa
 template <int D>
 __global__ void __launch_bounds__(kNTA) k_adj_flux(double* __restrict__ lam_out, const KParams p,
                                                     const AdjScalars* __restrict__ as, const double* __restrict__ F,
-                                                    double* __restrict__ part) {
+                                                    double* __restrict__ part,
+                                                    const double* __restrict__ WQ) {
   constexpr int NC = D + 2, Q = 2 * D;
   __shared__ double red[kNTA][5];
   const int cell = blockIdx.x * kNTA + threadIdx.x;
@@ -655,14 +701,14 @@ __global__ void __launch_bounds__(kNTA) k_adj_flux(double* __restrict__ lam_out,
     for (int k = 0; k < NC; ++k) {
       if (as->amax_cell[k] == cell) {
         const int a = as->amax_alpha[k];
-        const double q = F[(F_Q + 4 * a + k) * P + cell];
+        const double q = WQ[(F_Q + 4 * a + k) * P + cell];
         lQ[a][k] += (q > 0.0 ? 1.0 : (q < 0.0 ? -1.0 : 0.0)) * as->lamM[k];
       }
     }
     double W[NC], lW[NC], dprm[5];
 #pragma unroll
     for (int k = 0; k < NC; ++k) {
-      W[k] = F[(F_W + k) * P + cell];
+      W[k] = WQ[(F_W + k) * P + cell];
       lW[k] = F[(F_LWEQ + k) * P + cell];
     }
     const double lP = flux_vjp<D>(p, W, lQ, lu, lW, dprm);
@@ -790,29 +836,32 @@ int adj_part_entries(const KParams& p) { return (int)cells_blocks(p) + 1; }
 
 template <int D, class S>
 static cudaError_t adj_step_t(const AdjLaunch& A, const S* fin, int pulled, const double* lam_in, double* lam_out,
-                              long long n) {
+                              long long n, double* kept, bool kept_sensor) {
   const KParams& p = *A.p;
   const unsigned nb = cells_blocks(p);
   k_adj_set_step<<<1, 1, 0, A.stream>>>(A.as, A.sched, n);
-  k_adj_fields<D, S><<<nb, kNTA, 0, A.stream>>>(fin, p, pulled, A.as, A.F, A.pv, A.pi);
+  double* WQ = kept ? kept : A.F;  // planes F_W .. F_VORT of this step
+  if (kept) k_adj_argmax_kept<D><<<nb, kNTA, 0, A.stream>>>(kept, p, A.pv, A.pi);
+  else k_adj_fields<D, S><<<nb, kNTA, 0, A.stream>>>(fin, p, pulled, A.as, A.F, A.pv, A.pi);
   k_adj_argmax_fold<<<1, kNTA, 0, A.stream>>>(A.pv, A.pi, nb, p.nc, p.plane, A.as);
-  k_adj_sensor<D><<<nb, kNTA, 0, A.stream>>>(p, A.as, A.F);
-  k_adj_local<D, S><<<nb, kNTA, 0, A.stream>>>(fin, lam_in, lam_out, p, pulled, A.as, A.F);
-  k_adj_filter<D><<<nb, kNTA, 0, A.stream>>>(p, A.as, A.F, A.part);
+  if (!(kept && kept_sensor)) k_adj_sensor<D><<<nb, kNTA, 0, A.stream>>>(p, A.as, WQ, WQ);
+  k_adj_local<D, S><<<nb, kNTA, 0, A.stream>>>(fin, lam_in, lam_out, p, pulled, A.as, A.F, WQ);
+  k_adj_filter<D><<<nb, kNTA, 0, A.stream>>>(p, A.as, A.F, A.part, WQ);
   k_adj_fold<<<1, kNTA, 0, A.stream>>>(A.part, nb, p.nc, adj_field(A.as, offsetof(AdjScalars, lamM)), nullptr, 0);
-  k_adj_flux<D><<<nb, kNTA, 0, A.stream>>>(lam_out, p, A.as, A.F, A.part);
+  k_adj_flux<D><<<nb, kNTA, 0, A.stream>>>(lam_out, p, A.as, A.F, A.part, WQ);
   k_adj_fold<<<1, kNTA, 0, A.stream>>>(A.part, nb, 5, adj_field(A.as, offsetof(AdjScalars, eos)),
                                        adj_field(A.as, offsetof(AdjScalars, eos_comp)), 1);
   return cudaGetLastError();
 }
 
 cudaError_t adj_step(const AdjLaunch& A, int precision, const void* fin, int pulled, const double* lam_in, double* lam_out,
-                     long long n) {
+                     long long n, double* kept, bool kept_sensor) {
+  if (A.p->dim == 1) kept = nullptr;  // kept fields exist for 2D strips only
   if (precision == 0)
-    return A.p->dim == 1 ? adj_step_t<1, double>(A, (const double*)fin, pulled, lam_in, lam_out, n)
-                         : adj_step_t<2, double>(A, (const double*)fin, pulled, lam_in, lam_out, n);
-  return A.p->dim == 1 ? adj_step_t<1, float>(A, (const float*)fin, pulled, lam_in, lam_out, n)
-                       : adj_step_t<2, float>(A, (const float*)fin, pulled, lam_in, lam_out, n);
+    return A.p->dim == 1 ? adj_step_t<1, double>(A, (const double*)fin, pulled, lam_in, lam_out, n, kept, kept_sensor)
+                         : adj_step_t<2, double>(A, (const double*)fin, pulled, lam_in, lam_out, n, kept, kept_sensor);
+  return A.p->dim == 1 ? adj_step_t<1, float>(A, (const float*)fin, pulled, lam_in, lam_out, n, kept, kept_sensor)
+                       : adj_step_t<2, float>(A, (const float*)fin, pulled, lam_in, lam_out, n, kept, kept_sensor);
 }
 
 cudaError_t adj_terminal(const AdjLaunch& A, const double* dJ_dW, double* lam) {

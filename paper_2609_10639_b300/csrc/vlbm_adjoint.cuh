@@ -32,9 +32,12 @@ struct AdjLaunch {
 int adj_num_fields();
 int adj_part_entries(const KParams& p);
 // lambda^n from lambda^{n+1} for forward step n whose state f^n is `fin` (pulled or in place),
-// stored in FP64 (precision 0) or as FP32 deviations (precision 1)
+// stored in FP64 (precision 0) or as FP32 deviations (precision 1).  `kept`: 22 planes in the
+// layout of the workspace's first planes (W, u, Q, s_hat, s, theta, dil, vort) of f^n, the
+// first 14 stored by the maxima pass of the forward recomputation and, with kept_sensor, the
+// other 8 by its step kernel; nullptr to recompute them all.
 cudaError_t adj_step(const AdjLaunch& A, int precision, const void* fin, int pulled, const double* lam_in, double* lam_out,
-                     long long n);
+                     long long n, double* kept, bool kept_sensor);
 // lambda^N from dJ/dW(T); resets the EOS-gradient accumulator
 cudaError_t adj_terminal(const AdjLaunch& A, const double* dJ_dW, double* lam);
 // dJ/dW0 from lambda^0 through f^0 = f^eq(W0; c0); finishes the EOS-gradient sum

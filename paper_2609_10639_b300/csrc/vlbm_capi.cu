@@ -56,6 +56,8 @@ struct vlbm_s {
     size_t ckpt_states = 0;
     double* seg = nullptr;    // recomputed states of one segment
     size_t seg_states = 0;
+    double* kept = nullptr;   // FP64 strips: W, u, Q and sensor quantities of each recomputed state
+    size_t kept_cap = 0;
     double* lam[2] = {nullptr, nullptr};
     double* F = nullptr;      // workspace fields
     double* pv = nullptr;
@@ -403,6 +405,7 @@ vlbm_status vlbm_destroy(vlbm_t h) {
   cudaFree(h->fields);
   cudaFree(h->adj.ckpt);
   cudaFree(h->adj.seg);
+  cudaFree(h->adj.kept);
   cudaFree(h->adj.lam[0]);
   cudaFree(h->adj.lam[1]);
   cudaFree(h->adj.F);
@@ -788,6 +791,23 @@ vlbm_status vlbm_adjoint(vlbm_t h, const double* W0, int64_t n_steps, int32_t ch
   if (!grow(&A.ckpt, &A.ckpt_states, nseg * state) || !grow(&A.seg, &A.seg_states, segn * state) ||
       !grow(&A.sched, &A.sched_cap, (size_t)N + 1))
     return VLBM_E_NOMEM;
+  // FP64 strips: the recomputation keeps, for each state of a segment but the last, W, u, Q
+  // (stored by its maxima pass) and in sensor mode s_hat, s, theta, dil, vort (stored by its step
+  // kernel) in a slot of its own, which the adjoint of that step reads instead of recomputing
+  // them; used when the slots fit in half of the free device memory
+  bool use_kept = false;
+  const size_t kept_per_state = (size_t)22 * p.plane;
+  const bool kept_sensor = p.beta_mode == 0;
+  if (h->fields && p.dim == 2 && segn > 1) {
+    const size_t need = (segn - 1) * kept_per_state;
+    size_t fr = 0, tot = 0;
+    if (A.kept_cap >= need) {
+      use_kept = true;
+    } else if (cudaMemGetInfo(&fr, &tot) == cudaSuccess && need * sizeof(double) <= fr / 2) {
+      use_kept = grow(&A.kept, &A.kept_cap, need);
+    }
+    cudaGetLastError();
+  }
   if (!A.as) {
     if (cudaMalloc(&A.lam[0], lam_state * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&A.lam[1], lam_state * sizeof(double)) != cudaSuccess ||
@@ -848,6 +868,10 @@ vlbm_status vlbm_adjoint(vlbm_t h, const double* W0, int64_t n_steps, int32_t ch
         const int pulled = (n0 + j >= 1) ? 1 : 0;
         double* fin = A.seg + (size_t)j * state;
         double* fout = A.seg + (size_t)(j + 1) * state;
+        if (use_kept) {
+          FL.fields = A.kept + (size_t)j * kept_per_state;
+          FL.sens = kept_sensor ? FL.fields + (size_t)14 * p.plane : nullptr;
+        }
         VLBM_TRY(vlbm::launch_reduce(FL, h->precision, fin, pulled, true));
         VLBM_TRY(vlbm::launch_dt(FL));
         VLBM_TRY(vlbm::launch_step(FL, h->precision, false, fin, fout, pulled));
@@ -856,7 +880,9 @@ vlbm_status vlbm_adjoint(vlbm_t h, const double* W0, int64_t n_steps, int32_t ch
     }
     for (long long n = n1 - 1; n >= n0; --n) {
       const int pulled = n >= 1 ? 1 : 0;
-      VLBM_TRY(vlbm::adj_step(L, h->precision, A.seg + (size_t)(n - n0) * state, pulled, A.lam[li], A.lam[li ^ 1], n));
+      double* kept = (use_kept && n + 1 < n1) ? A.kept + (size_t)(n - n0) * kept_per_state : nullptr;
+      VLBM_TRY(vlbm::adj_step(L, h->precision, A.seg + (size_t)(n - n0) * state, pulled, A.lam[li], A.lam[li ^ 1], n,
+                              kept, kept_sensor));
       li ^= 1;
     }
   }

@@ -85,6 +85,8 @@ struct Launch {
   double* fields = nullptr;  // FP64 two-pass strips: W, u, Q of the current state, 14 planes
                              // [W0..3, u0, u1, Qx0..3, Qy0..3][y][x], written by the maxima pass
                              // and read by the step kernel (nullptr: not kept)
+  double* sens = nullptr;    // FP64 two-pass strips, adjoint recomputation only: the step kernel
+                             // also writes s_hat_0..3, s, theta, dil, vort of every cell (8 planes)
 };
 
 // precision: 0 = FP64, 1 = FP32 storage.  lookahead: fused single-kernel step.

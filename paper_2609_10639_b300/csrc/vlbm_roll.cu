@@ -62,7 +62,8 @@ template <class S, bool LOOK, int XW, int RR>
 __global__ void __launch_bounds__(XW * RR, sizeof(S) == 4 ? 1024 / (XW * RR) : 1) k_roll(const S* __restrict__ fin, S* __restrict__ fout,
                                                   Scalars* __restrict__ sc, const KParams p, const int pulled,
                                                   const typename Store<S>::M* __restrict__ invM_src,
-                                                  double* __restrict__ part, const double* __restrict__ fields) {
+                                                  double* __restrict__ part, const double* __restrict__ fields,
+                                                  double* __restrict__ sens) {
   using G = RollGeom<S, LOOK, XW, RR>;
   using M = typename G::M;
   constexpr int H = G::H, TXO = G::TXO, RQ = G::RQ, RS = G::RS, RF = G::RF;
@@ -179,11 +180,12 @@ __global__ void __launch_bounds__(XW * RR, sizeof(S) == 4 ? 1024 / (XW * RR) : 1
         ld4s(sQ + ((s0 * 2 + 0) * XW + tx - 1) * 4, qxm);
         ld4s(sQ + ((sp * 2 + 1) * XW + tx) * 4, qyp);
         ld4s(sQ + ((sm * 2 + 1) * XW + tx) * 4, qym);
-        M acc = 0;
+        M acc = 0, shk[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           const M jk = (qxp[k] - qxm[k]) + (qyp[k] - qym[k]);
           const M sh = jk * invMh[k];
+          shk[k] = sh;
           acc += sh * sh;
         }
         const M sval = sqrt_(acc);  // 2 s (Eq. 31); the 2 is folded into c_chi2
@@ -199,6 +201,19 @@ __global__ void __launch_bounds__(XW * RR, sizeof(S) == 4 ? 1024 / (XW * RR) : 1
         }
         const M dl = (uxp - uxm) + (vyp - vym), vt = (vxp - vxm) - (uyp - uym);  // 2 dx (dil, vort)
         const M th = div_(dl * dl, dl * dl + vt * vt + co.eps_lat);
+        if constexpr (sizeof(M) == 8) {
+          // adjoint recomputation: the sensor quantities of the cells this CTA owns, in the
+          // adjoint's units (s_hat_k, s, theta, dil, vort)
+          if (sens && r >= y0 && r < yend && px >= x0 && px < xend) {
+            const long long P = p.plane, c = (long long)r * p.nx + px;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) sens[k * P + c] = shk[k];
+            sens[4 * P + c] = 0.5 * sval;
+            sens[5 * P + c] = th;
+            sens[6 * P + c] = dl * p.inv2dx;
+            sens[7 * P + c] = vt * p.inv2dx;
+          }
+        }
         const int ss = ring<RS>(r, base);
         if constexpr (sizeof(M) == 8) {
           reinterpret_cast<double2*>(sS)[ss * XW + tx] = make_double2((double)sval, (double)th);
@@ -313,7 +328,7 @@ cudaError_t launch_roll_t(const Launch& L_, const void* fin, void* fout, int pul
   if (grid <= 0) return cudaErrorInitializationError;  // prepare_roll_kernels() not run on this device
   k_roll<S, LOOK, C::XW, C::RR><<<grid, G::NT, G::smem_bytes, L_.stream>>>(
       (const S*)fin, (S*)fout, L_.sc, p, pulled, (const typename Store<S>::M*)invM, L_.part,
-      (!LOOK && sizeof(S) == 8) ? L_.fields : nullptr);
+      (!LOOK && sizeof(S) == 8) ? L_.fields : nullptr, (!LOOK && sizeof(S) == 8) ? L_.sens : nullptr);
   return cudaGetLastError();
 }
 
