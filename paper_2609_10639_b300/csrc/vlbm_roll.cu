@@ -40,11 +40,16 @@ struct RollGeom {
   static constexpr int NT = XW * RR;
   static constexpr int RQ = 2 * RR;       // rows of the u/Q ring: [F-RR, F+RR)
   static constexpr int RS = RR + 2;       // rows of the (s, theta) ring: [F-RR-1, F+1)
-  static constexpr int RF = RR + 2;       // rows of the relaxed-population ring: [F-RR-2, F)
+  // Relaxed-population rings, one per direction, each as deep as the rows S4 still reads after
+  // S3 wrote rows [F-RR, F): x pairs and f*_{y-} (read at the row itself, or the row below it
+  // only where that is the edge row) [F-RR-1, F); f*_{y+} (read from the row above) [F-RR-2, F).
+  // The y- ring is one row short of the others: 4 resident CTAs per SM in FP32.
+  __host__ __device__ static constexpr int RF(int i) { return i == 2 ? RR + 1 : RR + 2; }
+  __host__ __device__ static constexpr int OF(int i) { return i <= 2 ? i * (RR + 2) : 2 * (RR + 2) + RR + 1; }
   static constexpr size_t nQ = (size_t)RQ * 2 * XW * 4;
   static constexpr size_t nU = (size_t)RQ * XW * 2;
   static constexpr size_t nS = (size_t)RS * XW * 2;
-  static constexpr size_t nF = LOOK ? (size_t)RF * 4 * XW * 4 : 0;
+  static constexpr size_t nF = LOOK ? (size_t)(OF(3) + RF(3)) * XW * 4 : 0;
   static constexpr size_t smem_bytes = (nQ + nU + nS + nF) * sizeof(M);
   static_assert(RR >= 2, "stage S2 of a block reads u/Q one row beyond it");
 };
@@ -66,7 +71,7 @@ __global__ void __launch_bounds__(XW * RR, sizeof(S) == 4 ? 1024 / (XW * RR) : 1
                                                   double* __restrict__ sens) {
   using G = RollGeom<S, LOOK, XW, RR>;
   using M = typename G::M;
-  constexpr int H = G::H, TXO = G::TXO, RQ = G::RQ, RS = G::RS, RF = G::RF;
+  constexpr int H = G::H, TXO = G::TXO, RQ = G::RQ, RS = G::RS;
   constexpr bool OFF = Store<S>::kOffset;
   if (!sc->active) return;
 
@@ -74,7 +79,7 @@ __global__ void __launch_bounds__(XW * RR, sizeof(S) == 4 ? 1024 / (XW * RR) : 1
   M* sQ = reinterpret_cast<M*>(smem_raw);  // [RQ][2][XW][4]
   M* sU = sQ + G::nQ;                      // [RQ][XW][2]
   M* sS = sU + G::nU;                      // [RS][XW][2]
-  M* sF = sS + G::nS;                      // [RF][4][XW][4]  (look-ahead)
+  M* sF = sS + G::nS;                      // direction i: [RF(i)][XW][4] from row OF(i) (look-ahead)
 
   const Coef<M>& co = coef<M>(p);
   const int tx = threadIdx.x % XW, ty = threadIdx.x / XW;
@@ -259,9 +264,11 @@ __global__ void __launch_bounds__(XW * RR, sizeof(S) == 4 ? 1024 / (XW * RR) : 1
         relax_cell<2, M>(fcar, Qc, beta, r_c, inv_c);
         if (r >= y0 && r < yend && px >= x0 && px < xend) store_cell<2, S, M>(fout, p, r * p.nx + px, fcar);
         if constexpr (LOOK) {
-          const int sf = ring<RF>(r, base);
-#pragma unroll
-          for (int i = 0; i < 4; ++i) st4s(sF + ((sf * 4 + i) * XW + tx) * 4, fcar[i]);
+          const int s4 = ring<G::RF(0)>(r, base), s3 = ring<G::RF(2)>(r, base);
+          st4s(sF + ((G::OF(0) + s4) * XW + tx) * 4, fcar[0]);
+          st4s(sF + ((G::OF(1) + s4) * XW + tx) * 4, fcar[1]);
+          st4s(sF + ((G::OF(2) + s3) * XW + tx) * 4, fcar[2]);
+          st4s(sF + ((G::OF(3) + s4) * XW + tx) * 4, fcar[3]);
         }
       }
     }
@@ -277,12 +284,12 @@ __global__ void __launch_bounds__(XW * RR, sizeof(S) == 4 ? 1024 / (XW * RR) : 1
       if (r >= y0 && r < yend && px >= x0 && px < xend) {
         M fr[4][4], W[4];
         const int xm = xi(-1), xp = xi(1);
-        const int sfy = ring<RF>(r, base);
-        const int sfm = ring<RF>(yc(r - 1), base), sfp = ring<RF>(yc(r + 1), base);
-        ld4s(sF + ((sfy * 4 + 0) * XW + xp) * 4, fr[0]);  // f*_{x-} from x+1
-        ld4s(sF + ((sfy * 4 + 1) * XW + xm) * 4, fr[1]);  // f*_{x+} from x-1
-        ld4s(sF + ((sfp * 4 + 2) * XW + tx) * 4, fr[2]);  // f*_{y-} from y+1
-        ld4s(sF + ((sfm * 4 + 3) * XW + tx) * 4, fr[3]);  // f*_{y+} from y-1
+        const int sfy = ring<G::RF(0)>(r, base);
+        const int sfm = ring<G::RF(3)>(yc(r - 1), base), sfp = ring<G::RF(2)>(yc(r + 1), base);
+        ld4s(sF + ((G::OF(0) + sfy) * XW + xp) * 4, fr[0]);  // f*_{x-} from x+1
+        ld4s(sF + ((G::OF(1) + sfy) * XW + xm) * 4, fr[1]);  // f*_{x+} from x-1
+        ld4s(sF + ((G::OF(2) + sfp) * XW + tx) * 4, fr[2]);  // f*_{y-} from y+1
+        ld4s(sF + ((G::OF(3) + sfm) * XW + tx) * 4, fr[3]);  // f*_{y+} from y-1
         moments<2, M, OFF>(fr, wq, W);
         M u[2], Qf[2][4], cs;
         bad |= !prim_flux<2, M, true>(p, W, u, Qf, cs);
