@@ -330,7 +330,7 @@ __global__ void __launch_bounds__(XW * RR, sizeof(S) == 4 ? 1024 / (XW * RR) : 1
 }
 
 // Strip shapes: XW columns per row (TXO = XW - 2H of them outputs), RR rows per iteration.
-// FP32 storage: 128 x 2 threads (rings of 4 rows, 56 KB, four CTAs per SM); measured on a B300
+// FP32 storage: 128 x 2 threads (rings of 3-4 rows, 54 KB, four CTAs per SM); measured on a B300
 // at 4096^2 the two-pass step kernel takes 0.42 ms this way against 0.46 ms with 128 x 4.
 // FP64: 128 x 4 threads, one CTA per SM.
 template <class S, bool LOOK>
