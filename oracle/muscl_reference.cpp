@@ -1,0 +1,146 @@
+// ORACLE: test infrastructure only.
+//
+// Independent reference solver for the one-dimensional benchmarks (Secs. IV B-IV D): a
+// second-order finite-volume method unrelated to the lattice Boltzmann scheme, of the kind the
+// paper validates against -- MUSCL reconstruction of the primitive variables (rho, u, P) with
+// the minmod limiter (van Leer 1979), the Rusanov (local Lax-Friedrichs) interface flux
+// (Rusanov 1961) and the two-stage second-order Runge-Kutta method of Heun (the strong-stability-
+// preserving form of Shu & Osher 1988).  The closure is the oracle's own equation of state
+// (orc_eos_eval, Eqs. 11-17), as the paper's reference solver uses the VLBM run's EOS routines.
+//
+// Readings (the paper names the method but not these details): the reference time step is
+// dt = CFL dx / max_j(|u_j| + c_j) with CFL = cfl (0.4 by default), taken from the state at the
+// start of the step, and the last step is shortened to land on t_end; boundaries are two ghost
+// cells per side, copies of the edge cell (zero gradient) or the periodic images; the interface
+// wave speed is max(|u_L| + c_L, |u_R| + c_R) of the two reconstructed states, with c^2 < 0 of a
+// reconstructed state (possible near the van der Waals spinodal) counted as 0.
+//
+// Pins: tests/test_oracle_muscl.py (the exact Riemann solution of the Sod problem, the second-
+// order convergence on a smooth periodic wave, conservation on a periodic domain).
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+extern "C" void orc_eos_eval(const double* eos6, double rho, double e, double* P, double* cs2);
+
+namespace {
+
+// Specific internal energy of (rho, P), the EOS solved for e: ideal gas e = P / ((gamma-1) rho)
+// (Eq. 15); van der Waals T = (P + a rho^2)(1 - b rho) / (R rho) from Eq. (16), then
+// e = cv T - a rho (Eq. 17).
+double energy_of(const double* e6, double rho, double P) {
+  if (e6[0] == 0.0) return P / ((e6[1] - 1.0) * rho);
+  const double a = e6[2], b = e6[3], R = e6[4], cv = e6[5];
+  const double T = (P + a * rho * rho) * (1.0 - b * rho) / (R * rho);
+  return cv * T - a * rho;
+}
+
+inline double minmod(double l, double r) {
+  if (l * r <= 0.0) return 0.0;
+  return std::fabs(l) < std::fabs(r) ? l : r;
+}
+
+struct Muscl {
+  const double* e6;
+  int n, bc;  // bc: 0 periodic, 1 zero gradient
+  double dx;
+  std::vector<double> V;  // primitives (rho, u, P) of n + 4 cells (two ghosts per side)
+
+  int ghost(int j) const {  // cell index of padded position j (0..n+3)
+    int i = j - 2;
+    if (i < 0) return bc == 0 ? i + n : 0;
+    if (i >= n) return bc == 0 ? i - n : n - 1;
+    return i;
+  }
+
+  // Primitives of every cell of U (3 x n, conserved); returns the largest |u| + c, or -1 if a
+  // cell is not physical (rho <= 0, c^2 <= 0 or non-finite).
+  double primitives(const std::vector<double>& U) {
+    double smax = 0.0;
+    bool bad = false;
+#pragma omp parallel for reduction(max : smax) reduction(|| : bad)
+    for (int i = 0; i < n; ++i) {
+      const double rho = U[i], m = U[n + i], E = U[2 * n + i];
+      const double u = m / rho, e = E / rho - 0.5 * u * u;
+      double P, c2;
+      orc_eos_eval(e6, rho, e, &P, &c2);
+      if (!(rho > 0.0) || !(c2 > 0.0) || !std::isfinite(P)) bad = true;
+      V[3 * (i + 2) + 0] = rho;
+      V[3 * (i + 2) + 1] = u;
+      V[3 * (i + 2) + 2] = P;
+      smax = std::max(smax, std::fabs(u) + std::sqrt(std::max(c2, 0.0)));
+    }
+    if (bad) return -1.0;
+    for (int j : {0, 1, n + 2, n + 3})
+      for (int k = 0; k < 3; ++k) V[3 * j + k] = V[3 * (ghost(j) + 2) + k];
+    return smax;
+  }
+
+  // Conserved state, flux and |u| + c of one primitive state.
+  void state(double rho, double u, double P, double* U, double* F, double* s) const {
+    const double e = energy_of(e6, rho, P);
+    double Pe, c2;
+    orc_eos_eval(e6, rho, e, &Pe, &c2);
+    const double E = rho * (e + 0.5 * u * u);
+    U[0] = rho, U[1] = rho * u, U[2] = E;
+    F[0] = rho * u, F[1] = rho * u * u + P, F[2] = (E + P) * u;
+    *s = std::fabs(u) + std::sqrt(std::max(c2, 0.0));
+  }
+
+  // L(U) = -(F_{i+1/2} - F_{i-1/2}) / dx for the primitives in V.
+  void rhs(std::vector<double>& L) const {
+    std::vector<double> Fh(3 * (n + 1));
+#pragma omp parallel for
+    for (int f = 0; f <= n; ++f) {  // interface between padded cells f+1 and f+2
+      const int jl = f + 1, jr = f + 2;
+      double vl[3], vr[3];
+      for (int k = 0; k < 3; ++k) {
+        const double sl = minmod(V[3 * jl + k] - V[3 * (jl - 1) + k], V[3 * (jl + 1) + k] - V[3 * jl + k]);
+        const double sr = minmod(V[3 * jr + k] - V[3 * (jr - 1) + k], V[3 * (jr + 1) + k] - V[3 * jr + k]);
+        vl[k] = V[3 * jl + k] + 0.5 * sl;
+        vr[k] = V[3 * jr + k] - 0.5 * sr;
+      }
+      double Ul[3], Ur[3], Fl[3], Fr[3], al, ar;
+      state(vl[0], vl[1], vl[2], Ul, Fl, &al);
+      state(vr[0], vr[1], vr[2], Ur, Fr, &ar);
+      const double a = std::max(al, ar);
+      for (int k = 0; k < 3; ++k) Fh[3 * f + k] = 0.5 * (Fl[k] + Fr[k]) - 0.5 * a * (Ur[k] - Ul[k]);
+    }
+#pragma omp parallel for
+    for (int i = 0; i < n; ++i)
+      for (int k = 0; k < 3; ++k) L[k * n + i] = -(Fh[3 * (i + 1) + k] - Fh[3 * i + k]) / dx;
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+// Advances the conserved field W (3 x n, [rho, rho u, rho E][x]) of a 1D problem on a uniform
+// grid of spacing dx from t = 0 to t_end.  Returns 0, or 1 if a non-physical state occurred
+// (W then holds the last physical state).  *steps receives the number of steps taken.
+int orc_muscl_1d(const double* e6, int n, double dx, int bc, double cfl, double t_end, double* W, long* steps) {
+  Muscl m{e6, n, bc, dx, std::vector<double>(3 * (n + 4))};
+  std::vector<double> U(W, W + 3 * n), U1(3 * n), L(3 * n);
+  double t = 0.0;
+  long s = 0;
+  while (t < t_end) {
+    const double smax = m.primitives(U);
+    if (smax < 0.0) break;
+    double dt = cfl * dx / smax;
+    const bool last = t + dt >= t_end;
+    if (last) dt = t_end - t;
+    m.rhs(L);
+    for (int j = 0; j < 3 * n; ++j) U1[j] = U[j] + dt * L[j];  // Heun stage 1
+    if (m.primitives(U1) < 0.0) break;
+    m.rhs(L);
+    for (int j = 0; j < 3 * n; ++j) U[j] = 0.5 * U[j] + 0.5 * (U1[j] + dt * L[j]);  // stage 2
+    t = last ? t_end : t + dt;
+    ++s;
+  }
+  *steps = s;
+  std::copy(U.begin(), U.end(), W);
+  return t < t_end ? 1 : 0;
+}
+
+}  // extern "C"

@@ -16,6 +16,7 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "vlbm_oracle.cpp")
+SRCS = [SRC, os.path.join(HERE, "muscl_reference.cpp")]
 LIB = os.path.join(HERE, "liboracle_vlbm.so")
 _lock = threading.Lock()
 _lib = None
@@ -25,8 +26,8 @@ BC_CODE = {"periodic": 0, "zerograd": 1}
 
 def build(force: bool = False) -> str:
     """Compile the oracle shared library next to its source (no fused multiply-add)."""
-    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
-        cmd = ["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", "-o", LIB, SRC]
+    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(s) for s in SRCS):
+        cmd = ["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", "-o", LIB, *SRCS]
         subprocess.run(cmd, check=True)
     return LIB
 
@@ -65,6 +66,7 @@ def lib():
                 "orc_dual_init": (I, [P, D, D]),
                 "orc_dual_step": (I, [P, Lg, C.POINTER(C.c_long)]),
                 "orc_dual_get_W": (None, [P, D, D]),
+                "orc_muscl_1d": (I, [D, I, C.c_double, I, C.c_double, C.c_double, D, C.POINTER(C.c_long)]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -266,3 +268,16 @@ def reproject(dim: int, c_old: float, c_new: float, f) -> np.ndarray:
     f = np.array(f, dtype=np.float64).reshape(-1).copy()
     lib().orc_reproject(dim, c_old, c_new, _dp(f))
     return f.reshape(2 * dim, dim + 2)
+
+
+def muscl_1d(eos: dict, W0, dx: float, bc: str, t_end: float, cfl: float = 0.4):
+    """The independent reference method (muscl_reference.cpp): MUSCL-minmod in primitive
+    variables, Rusanov flux, Heun RK2, from W0 (3 x n conserved) at t = 0 to t_end.  Returns
+    (W(t_end), steps)."""
+    W = np.ascontiguousarray(np.asarray(W0, dtype=np.float64).reshape(3, -1)).copy()
+    steps = C.c_long(0)
+    e6 = eos6(eos)
+    st = lib().orc_muscl_1d(_dp(e6), W.shape[1], dx, BC_CODE[bc], cfl, t_end, _dp(W), C.byref(steps))
+    if st:
+        raise ValueError(f"MUSCL reference: non-physical state after {steps.value} steps")
+    return W, steps.value

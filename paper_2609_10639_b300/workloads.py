@@ -90,7 +90,14 @@ BZT_2D = Problem("bzt_interface_2d_2048", 2, 2048, 2048, (0.0, 1.0, 0.0, 1.0), Z
 VORTEX_SCALE_2D = Problem("vortex_acoustic_2d_8192", 2, 8192, 8192, (0.0, 10.0, 0.0, 10.0), PER, IDEAL14, 0.5, 0.0, 2000)
 VORTEX_ADJOINT_2D = Problem("vortex_adjoint_2d_1024", 2, 1024, 1024, (0.0, 10.0, 0.0, 10.0), PER, IDEAL14, 0.5, 0.0, 1000)
 
-PROBLEMS = {p.name: p for p in (SOD_1D, QUADRANTS_2D, BZT_2D, VORTEX_SCALE_2D, VORTEX_ADJOINT_2D)}
+# One-dimensional accuracy benchmarks of Secs. IV B-IV D, run against the independent reference
+# solver: the strong shock tube (Sec. IV C, N = 2000, CFL 0.8) and the Shu-Osher problem
+# (Sec. IV B, x in [-5, 5], t = 1.9, CFL 0.8); the van der Waals shock tubes are argrow_1d().
+STRONG_SHOCK_1D = Problem("strong_shock_1d_2000", 1, 2000, 1, (0.0, 1.0, 0.0, 0.0), ZG, IDEAL14, 0.8, 0.012, 0)
+SHU_OSHER_1D = Problem("shu_osher_1d_2000", 1, 2000, 1, (-5.0, 5.0, 0.0, 0.0), ZG, IDEAL14, 0.8, 1.9, 0)
+
+PROBLEMS = {p.name: p for p in (SOD_1D, QUADRANTS_2D, BZT_2D, VORTEX_SCALE_2D, VORTEX_ADJOINT_2D, STRONG_SHOCK_1D,
+                                SHU_OSHER_1D)}
 
 
 def cell_centres(p: Problem):
@@ -342,11 +349,39 @@ def directions(p: Problem, count: int = 20, seed: int = 500, modes: int = 4) -> 
     return out
 
 
+def argrow_1d(case: dict, n: int = 1000) -> Problem:
+    """One of the van der Waals shock tubes of Sec. IV D (table of three cases): reduced units
+    a = 3, b = 1/3, R = 1, cv = R / (R/cv) of the case, x in [0, 1], CFL 0.8, run to the case's
+    t_end.  `case` holds the table's row: R_over_cv, rhoL, PL, rhoR, PR, t_end."""
+    eos = {"kind": "vdw", "a": 3.0, "b": 1.0 / 3.0, "R": 1.0, "cv": 1.0 / case["R_over_cv"]}
+    return Problem(f"argrow_{case['case']}_1d_{n}", 1, n, 1, (0.0, 1.0, 0.0, 0.0), ZG, eos, 0.8, case["t_end"], 0)
+
+
+def argrow_states(case: dict):
+    """(rho, u, P) left and right of the diaphragm at x = 0.5 (u = 0 on both sides)."""
+    return (case["rhoL"], 0.0, case["PL"]), (case["rhoR"], 0.0, case["PR"])
+
+
+def shu_osher_1d(p: Problem = SHU_OSHER_1D) -> np.ndarray:
+    """Shu-Osher shock / entropy-wave interaction (Sec. IV B): the post-shock state of a Mach 3
+    shock for x < -4, a sinusoidal density field 1 + 0.2 sin(5x) at rest with P = 1 ahead of it."""
+    X, _ = cell_centres(p)
+    L = X < -4.0
+    rho = np.where(L, 3.857143, 1.0 + 0.2 * np.sin(5.0 * X))
+    u = np.where(L, 2.629369, 0.0)
+    P = np.where(L, 10.33333, 1.0)
+    return conserved(p.eos, rho, [u], P)
+
+
 def initial_field(p: Problem) -> np.ndarray:
     """W0 of a named problem at its (possibly resized) grid."""
     base = p.name.split("@")[0]
     if base.startswith("sod_1d"):
         return sod_1d(p)
+    if base.startswith("strong_shock_1d"):
+        return sod_1d(p, left=(1.0, 0.0, 1000.0), right=(1.0, 0.0, 0.01))
+    if base.startswith("shu_osher_1d"):
+        return shu_osher_1d(p)
     if base.startswith("quadrants_2d"):
         return quadrants_2d(p)
     if base.startswith("bzt_interface_2d"):

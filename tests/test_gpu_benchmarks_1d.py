@@ -1,0 +1,102 @@
+"""GPU runs of the one-dimensional benchmarks of Secs. IV B-IV D at the paper's sizes.
+
+FP64: the CUDA path against the oracle on the same input -- relative max-norm of W within the
+100-step bar (1e-11) after 100 steps and within 1e-9 at the end of the full run (the bar of the
+full Sod run: thousands of steps through strong shocks let the rounding differences of the two
+summation orders grow) with the same step count and final time -- and the paper's printed
+accuracy numbers against the independent reference solver (the soft pins of
+test_oracle_benchmarks_1d.py, factor 3/2).  FP32 storage: the same printed numbers.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2609_10639_b300 import workloads as wl
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_numbers.json")))
+pytestmark = pytest.mark.gpu
+BAND = 1.5
+
+
+def rel_maxnorm(a, b):
+    num = np.abs(a - b).reshape(a.shape[0], -1).max(axis=1)
+    den = np.maximum(np.abs(b).reshape(b.shape[0], -1).max(axis=1), 1e-300)
+    return float((num / den).max())
+
+
+def pressure(eos, W):
+    rho = W[0]
+    u = W[1] / rho
+    e = W[2] / rho - 0.5 * u * u
+    return np.array([O.eos_eval(eos, r, ee)[0] for r, ee in zip(rho, e)])
+
+
+def coarse(a, n):
+    return a.reshape(n, -1).mean(axis=1)
+
+
+def workloads():
+    out = []
+    for c in GOLD["argrow_cases"]["cases"]:
+        prob = wl.argrow_1d(c, GOLD["argrow_cases"]["N"])
+        out.append((f"argrow_{c['case']}", prob, wl.sod_1d(prob, *wl.argrow_states(c)), {}))
+    out.append(("strong_shock", wl.STRONG_SHOCK_1D, wl.initial_field(wl.STRONG_SHOCK_1D), {}))
+    so = wl.SHU_OSHER_1D
+    out.append(("shu_osher_sensor", so, wl.shu_osher_1d(so), dict(beta_max=0.99)))
+    out.append(("shu_osher_const", so, wl.shu_osher_1d(so),
+                dict(beta_mode="const", beta_const=GOLD["shu_osher"]["beta_const_baseline"])))
+    return out
+
+
+WORKLOADS = workloads()
+
+
+@pytest.mark.parametrize("name,prob,W0,over", WORKLOADS, ids=[w[0] for w in WORKLOADS])
+def test_fp64_full_run_against_oracle(name, prob, W0, over):
+    from paper_2609_10639_b300 import vlbm
+
+    g = vlbm.Solver.for_problem(prob, **over)
+    o = O.OracleSolver.for_problem(prob, **over)
+    g.init(W0)
+    o.init(W0)
+    assert g.step(100) == 100 and o.step(100) == 100
+    assert rel_maxnorm(g.W().cpu().numpy(), o.W()) <= 1e-11
+    ng, no = g.step(10 ** 7, prob.t_end), o.step(10 ** 7, prob.t_end)
+    assert ng == no and g.time()[0] == prob.t_end == o.time()[0]
+    assert rel_maxnorm(g.W().cpu().numpy(), o.W()) <= 1e-9
+
+
+def reference(prob, make, n_ref):
+    ref_prob = prob.resized(n_ref)
+    Wr, _ = O.muscl_1d(prob.eos, make(ref_prob)[:, 0, :], ref_prob.dx, "zerograd", prob.t_end)
+    return Wr
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_store"])
+def test_printed_accuracy_numbers(precision):
+    from paper_2609_10639_b300 import vlbm
+
+    checks = []
+    for c in GOLD["argrow_cases"]["cases"]:
+        prob = wl.argrow_1d(c, GOLD["argrow_cases"]["N"])
+        checks.append((prob, lambda p, c=c: wl.sod_1d(p, *wl.argrow_states(c)), GOLD["argrow_cases"]["N_ref"],
+                       {"rho": c["L1_rho_vs_muscl"], "P": c["L1_P_vs_muscl"]}))
+    g = GOLD["strong_shock_tube"]
+    checks.append((wl.STRONG_SHOCK_1D, wl.initial_field, g["N_ref"],
+                   {"rho": g["L1_rho_vs_muscl"], "u": g["L1_u_vs_muscl"], "P": g["L1_P_vs_muscl"]}))
+    for prob, make, n_ref, printed in checks:
+        s = vlbm.Solver.for_problem(prob, precision=precision)
+        s.init(make(prob))
+        s.step(10 ** 7, prob.t_end)
+        assert s.time()[0] == prob.t_end
+        W = s.W().cpu().numpy()[:, 0, :]
+        Wr = reference(prob, make, n_ref)
+        got = {"rho": (W[0], Wr[0]), "u": (W[1] / W[0], Wr[1] / Wr[0]),
+               "P": (pressure(prob.eos, W), pressure(prob.eos, Wr))}
+        for key, value in printed.items():
+            a, b = got[key]
+            l1 = prob.dx * np.abs(a - coarse(b, prob.nx)).sum()
+            assert value / BAND <= l1 <= value * BAND, (prob.name, precision, key, l1, value)
