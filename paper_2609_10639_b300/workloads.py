@@ -96,8 +96,13 @@ VORTEX_ADJOINT_2D = Problem("vortex_adjoint_2d_1024", 2, 1024, 1024, (0.0, 10.0,
 STRONG_SHOCK_1D = Problem("strong_shock_1d_2000", 1, 2000, 1, (0.0, 1.0, 0.0, 0.0), ZG, IDEAL14, 0.8, 0.012, 0)
 SHU_OSHER_1D = Problem("shu_osher_1d_2000", 1, 2000, 1, (-5.0, 5.0, 0.0, 0.0), ZG, IDEAL14, 0.8, 1.9, 0)
 
+# Gresho vortex (Sec. IV A): periodic [0,1]^2, gamma = 5/3, the exact steady solution run to
+# t = 0.5 (CFL 0.5: the paper does not state it for this case).
+GRESHO_2D = Problem("gresho_2d_128", 2, 128, 128, (0.0, 1.0, 0.0, 1.0), PER, {"kind": "ideal", "gamma": 5.0 / 3.0}, 0.5,
+                    0.5, 0)
+
 PROBLEMS = {p.name: p for p in (SOD_1D, QUADRANTS_2D, BZT_2D, VORTEX_SCALE_2D, VORTEX_ADJOINT_2D, STRONG_SHOCK_1D,
-                                SHU_OSHER_1D)}
+                                SHU_OSHER_1D, GRESHO_2D)}
 
 
 def cell_centres(p: Problem):
@@ -373,6 +378,28 @@ def shu_osher_1d(p: Problem = SHU_OSHER_1D) -> np.ndarray:
     return conserved(p.eos, rho, [u], P)
 
 
+def gresho_primitives(p: Problem = GRESHO_2D, P0: float = 5.0):
+    """Exact steady Gresho vortex (Sec. IV A) about the domain centre: rho = 1, u_phi = 5r (r < 0.2),
+    2 - 5r (0.2 <= r < 0.4), 0 beyond; P = P0 + 12.5 r^2, + 4 (1 - 5r - ln 0.2 + ln r) in the ring,
+    P0 - 2 + 4 ln 2 outside.  Returns rho, u, v, P."""
+    X, Y = cell_centres(p)
+    x0, x1, y0, y1 = p.extent
+    dx_, dy_ = X - 0.5 * (x0 + x1), Y - 0.5 * (y0 + y1)
+    r = np.hypot(dx_, dy_)
+    rs = np.maximum(r, 1e-300)
+    uphi = np.where(r < 0.2, 5.0 * r, np.where(r < 0.4, 2.0 - 5.0 * r, 0.0))
+    ring = P0 + 12.5 * r * r + 4.0 * (1.0 - 5.0 * r - math.log(0.2) + np.log(rs))
+    P = np.where(r < 0.2, P0 + 12.5 * r * r, np.where(r < 0.4, ring, P0 - 2.0 + 4.0 * math.log(2.0)))
+    u = np.where(r > 0.0, -uphi * dy_ / rs, 0.0)
+    v = np.where(r > 0.0, uphi * dx_ / rs, 0.0)
+    return np.ones_like(X), u, v, P
+
+
+def gresho_2d(p: Problem = GRESHO_2D) -> np.ndarray:
+    rho, u, v, P = gresho_primitives(p)
+    return conserved(p.eos, rho, [u, v], P)
+
+
 def initial_field(p: Problem) -> np.ndarray:
     """W0 of a named problem at its (possibly resized) grid."""
     base = p.name.split("@")[0]
@@ -382,6 +409,8 @@ def initial_field(p: Problem) -> np.ndarray:
         return sod_1d(p, left=(1.0, 0.0, 1000.0), right=(1.0, 0.0, 0.01))
     if base.startswith("shu_osher_1d"):
         return shu_osher_1d(p)
+    if base.startswith("gresho_2d"):
+        return gresho_2d(p)
     if base.startswith("quadrants_2d"):
         return quadrants_2d(p)
     if base.startswith("bzt_interface_2d"):

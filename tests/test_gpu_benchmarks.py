@@ -1,11 +1,12 @@
-"""GPU runs of the one-dimensional benchmarks of Secs. IV B-IV D at the paper's sizes.
+"""GPU runs of the benchmarks of Secs. IV A-IV D at the paper's sizes (the 1D shock tubes and the
+Shu-Osher problem; the 2D Gresho vortex at 128^2).
 
 FP64: the CUDA path against the oracle on the same input -- relative max-norm of W within the
 100-step bar (1e-11) after 100 steps and within 1e-9 at the end of the full run (the bar of the
 full Sod run: thousands of steps through strong shocks let the rounding differences of the two
 summation orders grow) with the same step count and final time -- and the paper's printed
 accuracy numbers against the independent reference solver (the soft pins of
-test_oracle_benchmarks_1d.py, factor 3/2).  FP32 storage: the same printed numbers.
+test_oracle_benchmarks.py, factor 3/2).  FP32 storage: the same printed numbers.
 """
 import json
 import os
@@ -48,6 +49,7 @@ def workloads():
     out.append(("shu_osher_sensor", so, wl.shu_osher_1d(so), dict(beta_max=0.99)))
     out.append(("shu_osher_const", so, wl.shu_osher_1d(so),
                 dict(beta_mode="const", beta_const=GOLD["shu_osher"]["beta_const_baseline"])))
+    out.append(("gresho_128", wl.GRESHO_2D, wl.gresho_2d(wl.GRESHO_2D), {}))
     return out
 
 
