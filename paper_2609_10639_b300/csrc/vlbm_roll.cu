@@ -68,9 +68,10 @@ __device__ __forceinline__ int ring(int r, int base) {
 
 // FP32 storage: 1024 resident threads per SM (64 registers) to hide memory latency (0.46 vs
 // 0.73 ms per two-pass step kernel at 4096^2 with half of them); FP64 is bound by its FP64 pipe
-// and keeps one CTA of up to 128 registers per SM.
+// and runs two CTAs of up to 128 registers per SM, so that one CTA's stage S1 (loads only, with
+// W, u, Q kept by the maxima pass) overlaps the other's arithmetic.
 template <class S, bool LOOK, int XW, int RR>
-__global__ void __launch_bounds__(XW * RR, sizeof(S) == 4 ? 1024 / (XW * RR) : 1) k_roll(const S* __restrict__ fin, S* __restrict__ fout,
+__global__ void __launch_bounds__(XW * RR, sizeof(S) == 4 ? 1024 / (XW * RR) : 512 / (XW * RR)) k_roll(const S* __restrict__ fin, S* __restrict__ fout,
                                                   Scalars* __restrict__ sc, const KParams p, const int pulled,
                                                   const typename Store<S>::M* __restrict__ invM_src,
                                                   double* __restrict__ part, const double* __restrict__ fields,
@@ -332,10 +333,11 @@ __global__ void __launch_bounds__(XW * RR, sizeof(S) == 4 ? 1024 / (XW * RR) : 1
 // Strip shapes: XW columns per row (TXO = XW - 2H of them outputs), RR rows per iteration.
 // FP32 storage: 128 x 2 threads (rings of 3-4 rows, 54 KB, four CTAs per SM); measured on a B300
 // at 4096^2 the two-pass step kernel takes 0.42 ms this way against 0.46 ms with 128 x 4.
-// FP64: 128 x 4 threads, one CTA per SM.
+// FP64: 128 x 2 threads, two CTAs per SM (4.90 ms per two-pass step kernel at 4096^2 against
+// 5.26 ms with one CTA of 128 x 4, whose FP64 pipe idled while all its warps were in S1).
 template <class S, bool LOOK>
 struct RollCfg {
-  static constexpr int XW = 128, RR = sizeof(S) == 4 ? 2 : 4;
+  static constexpr int XW = 128, RR = 2;
 };
 
 constexpr int kMaxDevices = 64;
