@@ -299,6 +299,54 @@ __device__ __forceinline__ void relax_cell(M (&f)[2 * D][D + 2], const M (&Qc)[D
   }
 }
 
+// FP32 storage, D2Q4: the same two updates on component pairs (k = 0,1 and k = 2,3) with the
+// packed two-lane FP32 instructions of sm_100 and later (each lane rounds like the scalar
+// operation), halving the FP32 instruction count of the hottest arithmetic.  The moments keep the
+// scalar summation order ((f_x- + f_x+) + (f_y- + f_y+)) + W_ref/Q, so they are bit-identical.
+__device__ __forceinline__ float2 pk(float a, float b) { return make_float2(a, b); }
+
+template <>
+__device__ __forceinline__ void moments<2, float, true>(const float (&fr)[4][4], const float* wq, float (&W)[4]) {
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int k = 2 * h;
+    const float2 a = __fadd2_rn(pk(fr[0][k], fr[0][k + 1]), pk(fr[1][k], fr[1][k + 1]));
+    const float2 b = __fadd2_rn(pk(fr[2][k], fr[2][k + 1]), pk(fr[3][k], fr[3][k + 1]));
+    const float2 w = __fadd2_rn(__fadd2_rn(a, b), pk(wq[k], wq[k + 1]));
+    W[k] = w.x;
+    W[k + 1] = w.y;
+  }
+}
+
+template <>
+__device__ __forceinline__ void relax_cell<2, float>(float (&f)[4][4], const float (&Qc)[2][4], float beta, float r,
+                                                     float inv_c) {
+  const float om = 1.0f - 2.0f * beta;
+  const float bq = beta * inv_c;
+  const float omr = om * r * 0.5f;
+  const float omk = om * r * r * 0.25f;
+  const float2 cp = pk(0.25f + omk, 0.25f + omk), cm = pk(0.25f - omk, 0.25f - omk);
+  const float2 bq2 = pk(bq, bq), omr2 = pk(omr, omr), m1 = pk(-1.0f, -1.0f);
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int k = 2 * h;
+    const float2 f0 = pk(f[0][k], f[0][k + 1]), f1 = pk(f[1][k], f[1][k + 1]);
+    const float2 f2 = pk(f[2][k], f[2][k + 1]), f3 = pk(f[3][k], f[3][k + 1]);
+    const float2 sx = __fadd2_rn(f0, f1), sy = __fadd2_rn(f2, f3);
+    const float2 dx = __ffma2_rn(m1, f0, f1), dy = __ffma2_rn(m1, f2, f3);  // f+ - f-
+    const float2 gx = __ffma2_rn(bq2, pk(Qc[0][k], Qc[0][k + 1]), __fmul2_rn(omr2, dx));
+    const float2 gy = __ffma2_rn(bq2, pk(Qc[1][k], Qc[1][k + 1]), __fmul2_rn(omr2, dy));
+    const float2 wx = __ffma2_rn(cp, sx, __fmul2_rn(cm, sy));
+    const float2 wy = __ffma2_rn(cm, sx, __fmul2_rn(cp, sy));
+    const float2 o0 = __ffma2_rn(m1, gx, wx), o1 = __fadd2_rn(wx, gx);
+    const float2 o2 = __ffma2_rn(m1, gy, wy), o3 = __fadd2_rn(wy, gy);
+    f[0][k] = o0.x, f[0][k + 1] = o0.y;
+    f[1][k] = o1.x, f[1][k + 1] = o1.y;
+    f[2][k] = o2.x, f[2][k + 1] = o2.y;
+    f[3][k] = o3.x, f[3][k + 1] = o3.y;
+  }
+}
+
 // Separable (1/4, 1/2, 1/4) box filter (Sec. III D) without its normalisation: a + 2b + c.  Two
 // passes give 16 x the filtered value; the powers of two are exact, so scaling at the end
 // reproduces the normalised filter bit for bit.
