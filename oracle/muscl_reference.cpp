@@ -143,4 +143,117 @@ int orc_muscl_1d(const double* e6, int n, double dx, int bc, double cfl, double 
   return t < t_end ? 1 : 0;
 }
 
+// Two-dimensional form on an nx x ny grid of square cells (spacing dx), zero-gradient on every
+// side (two edge-copy ghost layers), without dimensional splitting: the same primitive minmod
+// reconstruction and Rusanov flux across every x face (speed |u| + c) and every y face
+// (|v| + c), summed into one update, Heun RK2 in time.  The step is
+// dt = cfl dx / max_cells(|u| + |v| + 2c), the sum form of the unsplit stability limit.
+// W is [rho, rho u, rho v, rho E][y][x].  Returns 0, or 1 if a non-physical state occurred.
+int orc_muscl_2d(const double* e6, int nx, int ny, double dx, double cfl, double t_end, double* W, long* steps) {
+  const long N = (long)nx * ny;
+  const int PX = nx + 4, PY = ny + 4;
+  std::vector<double> V((size_t)4 * PX * PY), U(W, W + 4 * N), U1(4 * N), L(4 * N);
+  auto vi = [&](int k, int y, int x) -> double& { return V[((size_t)k * PY + y) * PX + x]; };
+  // primitives with ghosts; returns max(|u| + |v| + 2c) or -1 if not physical
+  auto prim = [&](const std::vector<double>& Uc) -> double {
+    double smax = 0.0;
+    bool bad = false;
+#pragma omp parallel for reduction(max : smax) reduction(|| : bad)
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x) {
+        const long c = (long)y * nx + x;
+        const double rho = Uc[c], u = Uc[N + c] / rho, v = Uc[2 * N + c] / rho;
+        const double e = Uc[3 * N + c] / rho - 0.5 * (u * u + v * v);
+        double P, c2;
+        orc_eos_eval(e6, rho, e, &P, &c2);
+        if (!(rho > 0.0) || !(c2 > 0.0) || !std::isfinite(P)) bad = true;
+        vi(0, y + 2, x + 2) = rho, vi(1, y + 2, x + 2) = u, vi(2, y + 2, x + 2) = v, vi(3, y + 2, x + 2) = P;
+        smax = std::max(smax, std::fabs(u) + std::fabs(v) + 2.0 * std::sqrt(std::max(c2, 0.0)));
+      }
+    if (bad) return -1.0;
+    for (int k = 0; k < 4; ++k)
+      for (int y = 0; y < PY; ++y)
+        for (int x = 0; x < PX; ++x) {
+          const int sy = std::min(std::max(y, 2), ny + 1), sx = std::min(std::max(x, 2), nx + 1);
+          if (sy != y || sx != x) vi(k, y, x) = vi(k, sy, sx);
+        }
+    return smax;
+  };
+  // Rusanov flux across the face between padded cells a (left/below) and b, normal direction d
+  // (0: x, 1: y); (ya, xa) and the step (oy, ox) towards b give the four-cell stencil
+  auto face = [&](int ya, int xa, int oy, int ox, int d, double* F) {
+    double vl[4], vr[4];
+    for (int k = 0; k < 4; ++k) {
+      const double a0 = vi(k, ya - oy, xa - ox), a1 = vi(k, ya, xa), a2 = vi(k, ya + oy, xa + ox),
+                   a3 = vi(k, ya + 2 * oy, xa + 2 * ox);
+      vl[k] = a1 + 0.5 * minmod(a1 - a0, a2 - a1);
+      vr[k] = a2 - 0.5 * minmod(a2 - a1, a3 - a2);
+    }
+    double Ul[4], Ur[4], Fl[4], Fr[4], sl, sr;
+    for (int side = 0; side < 2; ++side) {
+      const double* q = side ? vr : vl;
+      double* Uo = side ? Ur : Ul;
+      double* Fo = side ? Fr : Fl;
+      const double e = energy_of(e6, q[0], q[3]);
+      double Pe, c2;
+      orc_eos_eval(e6, q[0], e, &Pe, &c2);
+      const double un = d == 0 ? q[1] : q[2];
+      const double E = q[0] * (e + 0.5 * (q[1] * q[1] + q[2] * q[2]));
+      Uo[0] = q[0], Uo[1] = q[0] * q[1], Uo[2] = q[0] * q[2], Uo[3] = E;
+      Fo[0] = q[0] * un, Fo[1] = q[0] * q[1] * un, Fo[2] = q[0] * q[2] * un, Fo[3] = (E + q[3]) * un;
+      Fo[1 + d] += q[3];
+      (side ? sr : sl) = std::fabs(un) + std::sqrt(std::max(c2, 0.0));
+    }
+    const double a = std::max(sl, sr);
+    for (int k = 0; k < 4; ++k) F[k] = 0.5 * (Fl[k] + Fr[k]) - 0.5 * a * (Ur[k] - Ul[k]);
+  };
+  // each face flux once: x faces (nx + 1 per row), y faces (ny + 1 per column)
+  std::vector<double> Fx((size_t)4 * ny * (nx + 1)), Fy((size_t)4 * (ny + 1) * nx);
+  auto rhs = [&]() {
+#pragma omp parallel for
+    for (int y = 0; y < ny; ++y)
+      for (int f = 0; f <= nx; ++f) {
+        double F[4];
+        face(y + 2, f + 1, 0, 1, 0, F);  // between cells f - 1 and f of row y
+        for (int k = 0; k < 4; ++k) Fx[((size_t)k * ny + y) * (nx + 1) + f] = F[k];
+      }
+#pragma omp parallel for
+    for (int g = 0; g <= ny; ++g)
+      for (int x = 0; x < nx; ++x) {
+        double F[4];
+        face(g + 1, x + 2, 1, 0, 1, F);  // between rows g - 1 and g of column x
+        for (int k = 0; k < 4; ++k) Fy[((size_t)k * (ny + 1) + g) * nx + x] = F[k];
+      }
+#pragma omp parallel for
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x) {
+        const long c = (long)y * nx + x;
+        for (int k = 0; k < 4; ++k) {
+          const double* fx = &Fx[((size_t)k * ny + y) * (nx + 1)];
+          const double* fy = &Fy[(size_t)k * (ny + 1) * nx];
+          L[k * N + c] = -((fx[x + 1] - fx[x]) + (fy[(size_t)(y + 1) * nx + x] - fy[(size_t)y * nx + x])) / dx;
+        }
+      }
+  };
+  double t = 0.0;
+  long s = 0;
+  while (t < t_end) {
+    const double smax = prim(U);
+    if (smax < 0.0) break;
+    double dt = cfl * dx / smax;
+    const bool last = t + dt >= t_end;
+    if (last) dt = t_end - t;
+    rhs();
+    for (long j = 0; j < 4 * N; ++j) U1[j] = U[j] + dt * L[j];
+    if (prim(U1) < 0.0) break;
+    rhs();
+    for (long j = 0; j < 4 * N; ++j) U[j] = 0.5 * U[j] + 0.5 * (U1[j] + dt * L[j]);
+    t = last ? t_end : t + dt;
+    ++s;
+  }
+  *steps = s;
+  std::copy(U.begin(), U.end(), W);
+  return t < t_end ? 1 : 0;
+}
+
 }  // extern "C"

@@ -67,6 +67,7 @@ def lib():
                 "orc_dual_step": (I, [P, Lg, C.POINTER(C.c_long)]),
                 "orc_dual_get_W": (None, [P, D, D]),
                 "orc_muscl_1d": (I, [D, I, C.c_double, I, C.c_double, C.c_double, D, C.POINTER(C.c_long)]),
+                "orc_muscl_2d": (I, [D, I, I, C.c_double, C.c_double, C.c_double, D, C.POINTER(C.c_long)]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -280,4 +281,17 @@ def muscl_1d(eos: dict, W0, dx: float, bc: str, t_end: float, cfl: float = 0.4):
     st = lib().orc_muscl_1d(_dp(e6), W.shape[1], dx, BC_CODE[bc], cfl, t_end, _dp(W), C.byref(steps))
     if st:
         raise ValueError(f"MUSCL reference: non-physical state after {steps.value} steps")
+    return W, steps.value
+
+
+def muscl_2d(eos: dict, W0, dx: float, t_end: float, cfl: float = 0.4):
+    """The reference method in 2D (muscl_reference.cpp): unsplit, zero-gradient sides, from W0
+    (4 x ny x nx conserved) at t = 0 to t_end.  Returns (W(t_end), steps)."""
+    W = np.ascontiguousarray(np.asarray(W0, dtype=np.float64)).copy()
+    _, ny, nx = W.shape
+    steps = C.c_long(0)
+    e6 = eos6(eos)
+    st = lib().orc_muscl_2d(_dp(e6), nx, ny, dx, cfl, t_end, _dp(W), C.byref(steps))
+    if st:
+        raise ValueError(f"MUSCL reference (2D): non-physical state after {steps.value} steps")
     return W, steps.value
