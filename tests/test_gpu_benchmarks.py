@@ -102,3 +102,63 @@ def test_printed_accuracy_numbers(precision):
             a, b = got[key]
             l1 = prob.dx * np.abs(a - coarse(b, prob.nx)).sum()
             assert value / BAND <= l1 <= value * BAND, (prob.name, precision, key, l1, value)
+
+
+def bilinear(f, m):
+    """Cell-centred field f (n x n on the unit square) interpolated bilinearly onto the m x m
+    cell centres (clamped to the outermost centres at the edges)."""
+    n = f.shape[0]
+    xc = (np.arange(m) + 0.5) / m * n - 0.5
+    i0 = np.clip(np.floor(xc).astype(int), 0, n - 2)
+    w = np.clip(xc - i0, 0.0, 1.0)
+    g = f[:, i0] * (1 - w) + f[:, i0 + 1] * w
+    return g[i0, :] * (1 - w)[:, None] + g[i0 + 1, :] * w[:, None]
+
+
+def riemann_2d_case(name):
+    import dataclasses
+
+    g = GOLD[name]
+    if name == "bzt_quadrants":
+        e = GOLD["bzt_vdw_eos"]
+        eos = {"kind": "vdw", "a": e["a"], "b": e["b"], "R": e["R"], "cv": e["R"] / (e["gamma"] - 1.0)}
+    else:
+        eos = wl.IDEAL14
+    base = dataclasses.replace(wl.QUADRANTS_2D, eos=eos, t_end=g["t_end"], name=f"{name}_2d")
+    return g, base.resized(g["N"]), base.resized(g["N_ref"])
+
+
+@pytest.fixture(scope="module")
+def riemann_2d_references():
+    """The unsplit reference solution at 1000^2 for each 2D case (host cores; about a minute)."""
+    out = {}
+    for name in ("laxliu_config12", "bzt_quadrants"):
+        g, _, pr = riemann_2d_case(name)
+        Wr, _ = O.muscl_2d(pr.eos, wl.quadrants_2d(pr, states=g["states_NE_NW_SW_SE"]), pr.dx, g["t_end"])
+        out[name] = Wr[0]
+    return out
+
+
+@pytest.mark.parametrize("name", ["laxliu_config12", "bzt_quadrants"])
+def test_2d_riemann_printed_accuracy_numbers(name, riemann_2d_references):
+    # Secs. IV E-IV F: the D2Q4 run at 800^2 interpolated onto the reference's 1000^2 grid;
+    # beta_max = 0.99 (with 1 the start-up pulses reach the zero-gradient boundaries undamped)
+    from paper_2609_10639_b300 import vlbm
+
+    g, p, pr = riemann_2d_case(name)
+    s = vlbm.Solver.for_problem(p, beta_max=0.99)
+    s.init(wl.quadrants_2d(p, states=g["states_NE_NW_SW_SE"]))
+    s.step(10 ** 7, g["t_end"])
+    assert s.time()[0] == g["t_end"]
+    W = s.W().cpu().numpy()
+    ref = riemann_2d_references[name]
+    d = np.abs(bilinear(W[0], pr.nx) - ref)
+    got = {"rel_L1_rho": d.sum() / np.abs(ref).sum(), "L2_rho": np.sqrt(np.mean(d * d)), "Linf_rho": d.max()}
+    for key, value in got.items():
+        assert g[key] / BAND <= value <= g[key] * BAND, (name, key, value, g[key])
+    if name == "bzt_quadrants":  # the flow stays in the BZT regime (Gamma < 0) almost everywhere
+        rho = W[0].ravel()
+        e = (W[3] / W[0] - 0.5 * ((W[1] / W[0]) ** 2 + (W[2] / W[0]) ** 2)).ravel()
+        idx = np.random.default_rng(0).integers(0, rho.size, 4000)
+        neg = np.mean([O.fundamental_derivative(p.eos, rho[i], e[i]) < 0.0 for i in idx])
+        assert neg >= g["gamma_negative_fraction"] - 0.02, neg
