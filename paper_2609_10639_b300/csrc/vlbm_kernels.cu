@@ -91,57 +91,68 @@ constexpr int kNTD = 1024;  // threads of the one-CTA scalar kernels
 
 __global__ void __launch_bounds__(kNTD) k_dt(Scalars* sc, const KParams p, const double* __restrict__ part,
                                               double* hist_dt, double* hist_c, const double* sched) {
+  // Every scalar the decision reads is loaded before the fold, as independent loads, so that
+  // their latencies overlap instead of forming a chain behind the fold (the kernel is
+  // latency-bound; nothing else writes these fields while it runs).
   const long long n = sc->n;
   const int slot = (int)(n & 1);
+  const int nparts = sc->nparts[slot];
+  const double t = sc->t, t_end = sc->t_end, c_prev = sc->c_prev;
+  const int done0 = sc->done, err0 = sc->err;
+  const long long sched_len = sc->sched_len, hist_cap = sc->hist_cap;
+  const double c_sched = (sched_len > 0 && n + 1 < sched_len) ? sched[n + 1] : 0.0;
   double mx[kNV];
-  fold_partials<kNTD>(part + (long long)slot * p.max_parts * kNV, sc->nparts[slot], mx);
+  fold_partials<kNTD>(part + (long long)slot * p.max_parts * kNV, nparts, mx);
   if (threadIdx.x != 0) return;
-  if (sc->t_end > 0.0 && sc->t >= sc->t_end) sc->done = 1;
-  if (sc->done || sc->err) {
+  const bool done = done0 || (t_end > 0.0 && t >= t_end);
+  if (done && !done0) sc->done = 1;
+  if (done || err0) {
     sc->active = 0;
     return;
   }
   const double smax = mx[0];
   double c;
-  if (sc->sched_len > 0) {
-    if (n + 1 >= sc->sched_len) {
-      sc->err |= ERR_SCHEDULE;
+  if (sched_len > 0) {
+    if (n + 1 >= sched_len) {
+      sc->err = err0 | ERR_SCHEDULE;
       sc->active = 0;
       return;
     }
-    c = sched[n + 1];
+    c = c_sched;
   } else {
     const bool retarget = p.retarget_every <= 1 || (n % p.retarget_every) == 0;
-    c = retarget ? smax / p.cfl : sc->c_prev;
+    c = retarget ? smax / p.cfl : c_prev;
   }
   double dt = p.dx / c;
   bool last = false;
-  if (sc->sched_len == 0 && sc->t_end > 0.0 && sc->t + dt >= sc->t_end) {  // land on t_end
-    dt = sc->t_end - sc->t;
+  if (sched_len == 0 && t_end > 0.0 && t + dt >= t_end) {  // land on t_end
+    dt = t_end - t;
     c = p.dx / dt;
     last = true;
   }
   if (!(c > 0.0) || !isfinite(c) || !(dt > 0.0)) {
-    sc->err |= ERR_NONPHYSICAL;
+    sc->err = err0 | ERR_NONPHYSICAL;
     sc->active = 0;
     return;
   }
+  const double r = c_prev / c, inv_c = 1.0 / c;
   sc->smax = smax;
-  sc->r = sc->c_prev / c;
+  sc->r = r;
   sc->c_new = c;
-  sc->inv_c = 1.0 / c;
+  sc->inv_c = inv_c;
   sc->dt = dt;
-  sc->r_f = (float)sc->r;
-  sc->inv_c_f = (float)sc->inv_c;
+  sc->r_f = (float)r;
+  sc->inv_c_f = (float)inv_c;
   for (int k = 0; k < p.nc; ++k) {
-    sc->inv_M[k] = mx[1 + k] > 0.0 ? 1.0 / mx[1 + k] : 0.0;
-    sc->inv_M_f[k] = (float)sc->inv_M[k];
+    const double im = mx[1 + k] > 0.0 ? 1.0 / mx[1 + k] : 0.0;
+    sc->inv_M[k] = im;
+    sc->inv_M_f[k] = (float)im;
   }
-  if (n < sc->hist_cap) {
+  if (n < hist_cap) {
     hist_dt[n] = dt;
     hist_c[n] = c;
   }
-  sc->t = last ? sc->t_end : sc->t + dt;
+  sc->t = last ? t_end : t + dt;
   sc->c_prev = c;
   sc->n = n + 1;
   sc->active = 1;
