@@ -8,16 +8,18 @@
 // recomputation is the x-halo of the strip (H columns on each side) and H rows at each end of a
 // segment, instead of a halo all around a small tile.  Per iteration (block start F):
 //
-//   S1  rows [F, F+RR):        pulled populations (Eq. 21), W, u, flux Q_alpha (Eqs. 10, 15-17)
+//   S1  rows [F, F+RR):        pulled populations (Eq. 21), W, u, flux Q_alpha (Eqs. 10, 15-17),
+//                              or in the FP64 two-pass form W, u, Q kept by the maxima pass
 //                              -> ring of Q and u (2 RR rows); the populations stay in registers
 //   S2  rows [F-RR+1, F+1):    flux-divergence activity s (Eqs. 28-31) and Ducros ratio theta
 //                              (Eqs. 32-33) -> ring of (s, theta) (RR + 2 rows)
 //   S3  rows [F-RR, F):        box filters and beta (Eqs. 34-35), fused reprojection (Eqs. 38-40)
 //                              and relaxation (Eqs. 20, 22) on the populations S1 loaded one
 //                              iteration earlier (same thread), single write to HBM
-//   S4  rows [F-RR-1, F-1):    (look-ahead) W^{n+1} = sum_i f*_i(x - sigma_i) from the ring of
-//                              relaxed populations (RR + 2 rows), and the maxima of the next
-//                              step (Eqs. 30, 36) accumulated in registers over the whole strip
+//   S4  rows [F-RR-1, F-1):    (look-ahead) W^{n+1} = sum_i f*_i(x - sigma_i) from the rings of
+//                              relaxed populations (RR + 2 rows, RR + 1 for f*_{y-}), and the
+//                              maxima of the next step (Eqs. 30, 36) accumulated in registers
+//                              over the whole strip
 //
 // Boundary rules as in the tile kernel: positions and rows outside a zero-gradient side hold the
 // edge cell's populations (S1 maps them), and every stencil read of s, theta (S3) and of the
