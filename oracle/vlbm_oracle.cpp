@@ -12,9 +12,10 @@
 // are the ones executed.
 //
 // Parity status: every function below is pinned by the CPU tests (closed forms, invariants,
-// the paper's printed numbers, brute force) except the exact per-cell values of the shock
-// sensor beta(x,t) (Sec. III D), for which the paper prints only two soft numbers (Sec. IV C);
-// beyond those and the invariants, beta is "parity unpinned".
+// the paper's printed numbers, brute force).  The shock sensor beta(x,t) (Sec. III D) is pinned
+// by closed forms on states where its chain is exact (a density ramp; the Ducros gate) and by the
+// paper's printed accuracy numbers; its exact per-cell values in general flows, for which the
+// paper prints only two soft numbers (Sec. IV C), are "parity unpinned".
 #include <algorithm>
 #include <cmath>
 #include <cstdint>

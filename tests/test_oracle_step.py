@@ -308,3 +308,46 @@ def test_nonphysical_state_is_rejected():
     s = O.OracleSolver.for_problem(prob)
     with pytest.raises(ValueError):
         s.init(W0)
+
+
+# --------------------------------------------------------------------------------------------
+# Shock sensor (Sec. III D, Eqs. 28-35) on states where its chain has a closed form.
+@pytest.mark.parametrize("g,c_sensor,clipped", [(0.5, 4.0, False), (40.0, 4.0, False), (0.5, 200.0, False), (0.5, 1000.0, True)])
+def test_sensor_a_closed_form_on_a_density_ramp(g, c_sensor, clipped):
+    # rho = rho0 + g x at constant u = U, P = P0 (ideal gas): every flux component is linear in
+    # rho (Q_0 = rho U, Q_1 = rho U^2 + P0, Q_2 = (P0/(gamma-1) + rho U^2/2 + P0) U), so the
+    # central jump j_k = dx g dQ_k/drho (U, U^2, U^3/2) is exact and the same in every interior
+    # cell, M_k = |Q_k| of the densest cell, s = sqrt(sum_k (j_k/M_k)^2 / 3) is constant, the
+    # normalised box filter leaves it unchanged away from the two edge cells, and
+    # beta = beta_max - (beta_max - beta_min) clip(C s, 0, 1).  A missing 1/2 in the jump, a local
+    # instead of global M_k, an unnormalised filter or a reversed map fails this.
+    n, rho0, U, P0, gam = 64, 1.0, 0.8, 1.5, 1.4
+    p = wl.SOD_1D.resized(n)
+    x = (np.arange(n) + 0.5) / n
+    rho = rho0 + g * x
+    W0 = wl.conserved(p.eos, rho, [np.full(n, U)], np.full(n, P0))
+    s = O.OracleSolver.for_problem(p, threads=1, c_sensor=c_sensor)
+    s.init(W0)
+    beta = s.eval_beta()[0]
+    dx, rmax = p.dx, rho.max()
+    j = dx * g * np.array([U, U * U, 0.5 * U ** 3])
+    M = np.array([rmax * U, rmax * U * U + P0, (P0 / (gam - 1.0) + 0.5 * rmax * U * U + P0) * U])
+    s_val = math.sqrt(np.sum((j / M) ** 2) / 3.0)
+    chi = min(max(c_sensor * s_val, 0.0), 1.0)
+    assert (chi == 1.0) == clipped
+    expect = p.beta_max - (p.beta_max - p.beta_min) * chi
+    assert np.abs(beta[2:-2] - expect).max() <= 1e-13
+
+
+def test_sensor_b_is_gated_by_the_ducros_ratio():
+    # 2D: the same ramp along x (uniform in y, velocity along x constant) has no dilatation and no
+    # vorticity, so theta = 0 (Eq. 33) and beta = beta_max everywhere, although the flux activity
+    # alone would lower it; a pure shear v = V x (vorticity, no dilatation) also gives theta = 0.
+    n = 32
+    p = wl.QUADRANTS_2D.resized(n)
+    X, Y = wl.cell_centres(p)
+    for vel in ([np.full_like(X, 0.8), np.zeros_like(X)], [np.zeros_like(X), 0.3 * X]):
+        W0 = wl.conserved(p.eos, 1.0 + 40.0 * X, vel, np.full_like(X, 1.5))
+        s = O.OracleSolver.for_problem(p, threads=1)
+        s.init(W0)
+        assert np.array_equal(s.eval_beta(), np.full((n, n), p.beta_max))
