@@ -287,8 +287,10 @@ def oracle_sample(min_seconds=10.0, n=1024, chunk=5, max_steps=None):
     s = O.OracleSolver.for_problem(p)
     s.init(wl.quadrants_2d(p))
     steps, t0 = 0, time.perf_counter()
-    while time.perf_counter() - t0 < min_seconds and (max_steps is None or steps < max_steps):
-        steps += s.step(chunk)
+    while max_steps is None or steps < max_steps:  # at least one chunk, then until min_seconds
+        if steps > 0 and time.perf_counter() - t0 >= min_seconds:
+            break
+        steps += s.step(chunk if max_steps is None else min(chunk, max_steps - steps))
     dt = time.perf_counter() - t0
     return {"value": p.ncells * steps / dt / 1e6, "unit": UNIT, "cores": s.threads, "kind": "oracle",
             "sample": f"quadrants_2d seed input at {n}x{n}, {steps} FP64 steps from t=0, {dt:.1f} s of CPU work"}

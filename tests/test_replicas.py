@@ -55,3 +55,26 @@ def test_reference_arm_is_silent_on_other_ranks(monkeypatch):
     with redirect_stdout(buf):
         bench.run_reference(A())
     assert buf.getvalue() == ""
+
+
+def test_reference_arm_line_on_rank_zero(monkeypatch):
+    # the oracle timed on a bounded sample: a positive throughput, the keys of the JSON line
+    sys.path.insert(0, ROOT)
+    import json
+
+    import bench
+
+    monkeypatch.setenv("WORLD_SIZE", "1")
+    monkeypatch.setenv("RANK", "0")
+
+    class A:
+        steps, warmup = 1, 1
+
+    buf = io.StringIO()
+    with redirect_stdout(buf):
+        bench.run_reference(A())
+    line = json.loads(buf.getvalue().strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0.0
+    assert line["cpu_baseline"]["value"] == line["value"] and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+    assert "4 FP64 steps" in line["cpu_baseline"]["sample"]
