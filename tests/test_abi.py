@@ -58,3 +58,25 @@ def test_create_rejects_bad_arguments_without_touching_the_gpu():
     assert L.vlbm_create(C.byref(g), C.byref(e), C.byref(p), None, C.byref(h)) == vlbm.E_INVAL
     assert L.vlbm_step(None, 1, 0.0, None) == vlbm.E_INVAL
     assert L.vlbm_destroy(None) == vlbm.OK
+
+
+def test_kernel_digest_ignores_comments(tmp_path, monkeypatch):
+    # the digest that ties the committed ncu counters to the kernels changes with the code, not
+    # with its comments
+    import shutil
+    import sys
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    csrc = tmp_path / "paper_2609_10639_b300" / "csrc"
+    csrc.mkdir(parents=True)
+    for name in ("vlbm_device.cuh", "vlbm_kernels.cu", "vlbm_roll.cu"):
+        shutil.copy(os.path.join(ROOT, "paper_2609_10639_b300", "csrc", name), csrc / name)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    d0 = bench.kernels_sha()
+    roll = csrc / "vlbm_roll.cu"
+    roll.write_text("// a comment line\n" + roll.read_text().replace("{", "{  /* inline */", 1))
+    assert bench.kernels_sha() == d0
+    roll.write_text(roll.read_text() + "\nstatic int unused_symbol = 1;\n")
+    assert bench.kernels_sha() != d0
