@@ -51,6 +51,7 @@ def lib():
                 "orc_set_state": (None, [P, D, C.c_double, C.c_double, Lg]),
                 "orc_get_beta": (None, [P, D]),
                 "orc_eval_beta": (I, [P, D]),
+                "orc_eval_sensor_fields": (I, [P, D, D, D, D, D]),
                 "orc_get_time": (None, [P, D, C.POINTER(C.c_long), D]),
                 "orc_get_hist": (Lg, [P, D, D, Lg]),
                 "orc_set_schedule": (None, [P, D, Lg]),
@@ -166,6 +167,15 @@ class OracleSolver:
         st = self.L.orc_eval_beta(self.h, _dp(out))
         if st:
             raise ValueError("oracle eval_beta: non-physical state")
+        return out
+
+    def sensor_fields(self) -> dict:
+        """The shock sensor's fields of the current state (no step taken): s and theta before
+        the box filter, s_bar and theta_bar after it, and beta (theta = 0 in 1D)."""
+        out = {k: np.empty((self.ny, self.nx)) for k in ("s", "theta", "s_bar", "theta_bar", "beta")}
+        st = self.L.orc_eval_sensor_fields(self.h, *[_dp(out[k]) for k in ("s", "theta", "s_bar", "theta_bar", "beta")])
+        if st:
+            raise ValueError("oracle sensor_fields: non-physical state")
         return out
 
     def time(self):

@@ -13,9 +13,10 @@
 //
 // Parity status: every function below is pinned by the CPU tests (closed forms, invariants,
 // the paper's printed numbers, brute force).  The shock sensor beta(x,t) (Sec. III D) is pinned
-// by closed forms on states where its chain is exact (a density ramp; the Ducros gate) and by the
-// paper's printed accuracy numbers; its exact per-cell values in general flows, for which the
-// paper prints only two soft numbers (Sec. IV C), are "parity unpinned".
+// by closed forms on states where its chain is exact: a density ramp (activity, normalisation,
+// beta map), slope kinks of the density and of the velocity (the (1/4, 1/2, 1/4) filter along
+// each axis applied to s and to the Ducros ratio theta, theta itself, and the gate s_bar theta_bar),
+// and the Ducros gate on shear; and by the paper's printed accuracy numbers.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -225,6 +226,8 @@ struct Solver {
   Eos<T> eos;
   Params prm;
   std::vector<T> f, fnext, W, u, P, cs2, Qf, s, th, tmp, beta;
+  std::vector<T> s_raw, th_raw;  // s and theta before the filter (kept only on request)
+  bool keep_raw = false;
   double c_prev = 0, t = 0;
   long n = 0;
   std::vector<double> hist_dt, hist_c, sched;
@@ -353,6 +356,10 @@ struct Solver {
           th[c] = dil * dil / (dil * dil + vort * vort + prm.ducros_eps);
         }
       }
+    if (keep_raw) {
+      s_raw = s;
+      th_raw = th;
+    }
     box_filter(s);  // s_bar = S[s]
     if (D == 2) box_filter(th);  // theta_bar = S[theta]
     // Sensor A (1D, Eq. 34) / Sensor B (2D, Eq. 35).
@@ -608,6 +615,24 @@ int orc_eval_beta(void* h, double* b) {
   if (s->moments_and_flux()) return E_NONPHYSICAL;
   s->sensor();
   for (long c = 0; c < s->N; ++c) b[c] = s->beta[c];
+  return OK;
+}
+// The shock sensor's fields of the current state (diagnostic for the pins): the activity s and
+// the Ducros ratio theta before the box filter, their filtered values s_bar and theta_bar, and
+// beta (Eqs. 31, 33-35).  1D: theta and theta_bar are returned as 0 (Sensor A has no gate).
+int orc_eval_sensor_fields(void* h, double* s_out, double* th_out, double* sbar_out, double* thbar_out, double* b) {
+  auto* s = static_cast<Solver<double>*>(h);
+  if (s->moments_and_flux()) return E_NONPHYSICAL;
+  s->keep_raw = true;
+  s->sensor();
+  s->keep_raw = false;
+  for (long c = 0; c < s->N; ++c) {
+    s_out[c] = s->s_raw[c];
+    th_out[c] = s->D == 2 ? s->th_raw[c] : 0.0;
+    sbar_out[c] = s->s[c];
+    thbar_out[c] = s->D == 2 ? s->th[c] : 0.0;
+    b[c] = s->beta[c];
+  }
   return OK;
 }
 void orc_get_time(void* h, double* t, long* n, double* c_prev) {
