@@ -48,7 +48,7 @@ FP64_FLOPS_STEP_KERNEL = 178
 # Algorithmic bytes of one adjoint step including the recomputation of the forward state (FP64):
 # recompute 256 + read the forward state 128 + read lambda 128 + write lambda 128.
 ADJ_BYTES_PER_CELL = 640
-SMS, FP64_FMA_PER_CLK_PER_SM = 148, 2
+FP64_FMA_PER_CLK_PER_SM = 2  # B300 FP64 unit count per SM (nominal figure, for context)
 
 
 def peaks():
@@ -60,9 +60,13 @@ def peaks():
         return {"hbm_gbs": 6400.0, "sm_max_mhz": 2032.0, "source": "fallback"}
 
 
-def fp64_peak_tflops(sm_mhz):
-    """Dense FP64 peak from unit counts and clock: 148 SMs x 2 FP64 FMA/clk x 2 flop x f_SM."""
-    return SMS * FP64_FMA_PER_CLK_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+def fp64_nominal_tflops(sm_mhz):
+    """Dense FP64 rate from unit counts and clock: SMs (of this device) x 2 FP64 FMA/clk x 2 flop x
+    f_SM.  Context only; the roofline uses the measured rate."""
+    import torch
+
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    return sms * FP64_FMA_PER_CLK_PER_SM * 2 * sm_mhz * 1e6 / 1e12
 
 
 class ClockSampler:
@@ -114,13 +118,17 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# Sources of the step kernels (csrc/), digested by kernels_sha().
+KERNEL_SOURCES = ("vlbm_internal.cuh", "vlbm_device.cuh", "vlbm_kernels.cu", "vlbm_roll.cu")
+
+
 def kernels_sha():
     """Digest of the step-kernel code (the counters in profiles/ are tied to it): the sources with
     comments and blank lines removed, so that a comment edit does not invalidate the counters."""
     import re
 
     h = hashlib.sha256()
-    for name in ("vlbm_device.cuh", "vlbm_kernels.cu", "vlbm_roll.cu"):
+    for name in KERNEL_SOURCES:
         src = open(os.path.join(ROOT, "paper_2609_10639_b300", "csrc", name)).read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
         lines = [re.sub(r"//.*$", "", ln).rstrip() for ln in src.splitlines()]
@@ -277,14 +285,14 @@ def time_adjoint(n_steps, K, world):
     return {"fwd_ms": fwd_ms, "rev_ms": rev_ms, "rec_ms": rec_ms, "cells": prob.ncells, "steps": n_steps, "K": K}
 
 
-def oracle_sample(min_seconds=10.0, n=1024, chunk=5, max_steps=None):
+def oracle_sample(min_seconds=10.0, n=1024, chunk=5, max_steps=None, threads=None):
     """The oracle (as it stands) on a bounded sample of the workload: the same input generator at
     n x n cells, stepped in chunks until min_seconds of CPU work (or max_steps) have run."""
     from oracle import oracle as O
     from paper_2609_10639_b300 import workloads as wl
 
     p = wl.QUADRANTS_2D.resized(n)
-    s = O.OracleSolver.for_problem(p)
+    s = O.OracleSolver.for_problem(p, threads=threads)
     s.init(wl.quadrants_2d(p))
     steps, t0 = 0, time.perf_counter()
     while max_steps is None or steps < max_steps:  # at least one chunk, then until min_seconds
@@ -296,28 +304,47 @@ def oracle_sample(min_seconds=10.0, n=1024, chunk=5, max_steps=None):
             "sample": f"quadrants_2d seed input at {n}x{n}, {steps} FP64 steps from t=0, {dt:.1f} s of CPU work"}
 
 
-def run_reference(args):
-    """The reference arm: the oracle timed on the host cores, same metric and workload."""
+def cpu_baselines():
+    """The oracle on all host cores (10 s sample) and on one core (4 s sample)."""
+    allc = oracle_sample(min_seconds=10.0)
+    one = oracle_sample(min_seconds=4.0, n=512, chunk=2, threads=1)
+    allc["one_core"] = {"value": one["value"], "unit": UNIT, "cores": 1, "sample": one["sample"]}
+    return allc
+
+
+def run_reference(args, n=1024, steps_per_step=8):
+    """The reference arm: the oracle timed on the host cores, same metric and workload.  One oracle
+    solver is built and warmed up once; each timed step advances it by `steps_per_step` time steps
+    of the n x n copy of the workload's input."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if world > 1 and rank != 0:
         return
+    from oracle import oracle as O
     from paper_2609_10639_b300 import workloads as wl
 
+    p = wl.QUADRANTS_2D.resized(n)
+    s = O.OracleSolver.for_problem(p)
+    s.init(wl.quadrants_2d(p))
     for _ in range(args.warmup):
-        oracle_sample(min_seconds=0.0, max_steps=2, chunk=2)
-    vals, t0 = [], time.perf_counter()
+        s.step(1)
+    times = []
     for _ in range(args.steps):
-        vals.append(oracle_sample(min_seconds=0.0, max_steps=4, chunk=4))
-    total = time.perf_counter() - t0
-    value = statistics.median(v["value"] for v in vals)
+        t0 = time.perf_counter()
+        done = s.step(steps_per_step)
+        times.append(time.perf_counter() - t0)
+        assert done == steps_per_step
+    total = sum(times)
+    value = p.ncells * steps_per_step * args.steps / total / 1e6
+    sample = (f"quadrants_2d seed input at {n}x{n}, one solver, {args.warmup} warm-up steps then {args.steps} x "
+              f"{steps_per_step} FP64 steps, {total:.1f} s of CPU work")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl.QUADRANTS_2D.name, "sample": "1024x1024 copy of the input, 4 steps per step",
+            "config": {"workload": wl.QUADRANTS_2D.name,
+                       "sample": f"{n}x{n} copy of the input, {steps_per_step} time steps per step",
                        "parallelism": "host cores (OpenMP)"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": vals[0]["cores"], "kind": "oracle",
-                             "sample": vals[0]["sample"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": s.threads, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -360,6 +387,7 @@ def run_ours(args):
     pk = peaks()
     cells = prob.ncells
 
+    fp64_peak = vlbm.measure_fp64_peak(5)  # TFLOP/s, measured on this GPU just before the timed region
     r64 = time_path(prob, W0, "fp64", S, K, Wm, world, clocks_idx=local)
     mlups64 = aggregate_mlups(world, cells, S * K, r64["ms"])
     r32 = time_path(prob, W0, "fp32_store", S, K, Wm, world)
@@ -377,12 +405,12 @@ def run_ours(args):
     k64_s = r64["kernel_ms_avg"] * 1e-3
     k32_s = r32["kernel_ms_avg"] * 1e-3
     fp64_ach = FP64_FLOPS_STEP_KERNEL * cells / k64_s / 1e12
-    fp64_peak = fp64_peak_tflops(pk["sm_max_mhz"])
+    fp64_nominal = fp64_nominal_tflops(pk["sm_max_mhz"])
     hbm64 = FP64_STEP_KERNEL_BYTES * cells / k64_s / 1e9
     hbm32 = BYTES_PER_CELL["fp32_store"] * cells / k32_s / 1e9
     t64 = kernel_traffic("fp64_step")
     t32 = kernel_traffic("fp32_store_step")
-    cpu = oracle_sample(min_seconds=10.0) if world == 1 else None
+    cpu = cpu_baselines() if world == 1 else None
     launches = K * (S * r64["launches_per_step"] + 1)
     line = {
         "metric": METRIC, "value": mlups64, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": Wm,
@@ -396,7 +424,9 @@ def run_ours(args):
                      "frac": fp64_ach / fp64_peak, "traffic": None if t64 is None else t64 * cells,
                      "kernel": "k_roll<double> (FP64 step kernel, column strips, two-pass form)",
                      "kernel_ms": r64["kernel_ms_avg"], "flops_per_cell": FP64_FLOPS_STEP_KERNEL,
-                     "peak_source": "FP64 unit count x max SM clock", "hbm_achieved_gbs": hbm64,
+                     "peak_source": "measured: vlbm_measure_fp64_peak (chains of dependent FP64 FMAs on every "
+                                    "SM, best of 5 launches, just before the timed region)",
+                     "peak_nominal": fp64_nominal, "hbm_achieved_gbs": hbm64,
                      "hbm_frac": hbm64 / pk["hbm_gbs"], "hbm_peak_source": pk["source"]},
         "variants": {
             "fp32_store": {"value": mlups32, "unit": UNIT, "dtype": "f32 storage (FP32 math, FP64 maxima)",

@@ -174,10 +174,14 @@ vlbm_status vlbm_load_state(vlbm_t h, const void* host, size_t n_bytes);
  * must have been initialised. */
 vlbm_status vlbm_time_step_kernel(vlbm_t h, int32_t reps, double* ms_per_launch);
 
-/* Live kernel timing.  With `on` != 0, vlbm_step issues its steps one by one (no CUDA graph) and
- * brackets every launch of the dominant step kernel with a pair of CUDA events on the handle's
- * stream; vlbm_get_profile then returns the summed device time of those launches (ms) and their
- * count, and resets both (synchronises).  Turning profiling on or off also resets them. */
+/* Live kernel timing.  With `on` != 0, every launch of the dominant step kernel by vlbm_step is
+ * bracketed by a pair of CUDA events on the handle's stream: the graph chunks vlbm_step launches
+ * are then captured with an event-record node before and after each step-kernel launch (the same
+ * kernels, the same launches), and steps issued outside a chunk get an event pair each.  The
+ * events of a chunk are read when vlbm_step synchronises at its end; a call that launches more
+ * than one chunk synchronises once before each further chunk to read them.  vlbm_get_profile
+ * returns the summed device time of the bracketed launches (ms) and their count, and resets both
+ * (synchronises).  Turning profiling on or off also resets them. */
 vlbm_status vlbm_set_profiling(vlbm_t h, int32_t on);
 vlbm_status vlbm_get_profile(vlbm_t h, double* ms_total, int64_t* launches);
 
@@ -233,9 +237,11 @@ vlbm_status vlbm_launches_per_step(vlbm_t h, int32_t* launches);
  *   cuda_stream: stream for the work (NULL: legacy default stream); the call returns without
  *             waiting, beta is valid once the stream reaches this point.
  *
- * Limits and behaviour: at most 2,097,152 cells (nx ny); larger grids return VLBM_E_INVAL.  The
- * first call on a device looks up the array's device address (cudaGetSymbolAddress) and sets the
- * kernels' shared-memory attribute; make that first call before any stream capture.  The call
+ * Limits and behaviour: at most 2,097,152 cells (nx ny, each axis checked first); larger grids
+ * return VLBM_E_INVAL.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and sets the kernels' shared-memory attribute, under a lock, so host
+ * threads may make their first calls concurrently; make that first call before any stream
+ * capture.  The call
  * allocates nothing (no cudaMalloc, cudaFree or allocating library routine).  Every call on a
  * device shares the one array and leaves its contents behind; the call clears the scalar block
  * at its start, and every other entry it reads it writes first.  Calls that overlap on the GPU
@@ -243,6 +249,13 @@ vlbm_status vlbm_launches_per_step(vlbm_t h, int32_t* launches);
  * non-physical state is not reported (use a handle for that); beta is then meaningless. */
 vlbm_status vlbm_beta_noalloc(const vlbm_grid* grid, const vlbm_eos* eos, const vlbm_params* params, const double* f,
                               int32_t in_place, double* beta, void* cuda_stream);
+
+/* Measured FP64 throughput of the current GPU, the denominator of the FP64 step's ALU roofline
+ * (the method has no counterpart; a measurement aid).  Runs `reps` timed launches of a kernel in
+ * which every thread advances eight independent chains of dependent FP64 fused multiply-adds, on
+ * a grid that fills every SM, and writes the best rate in TFLOP/s (an FMA counted as 2 flops) to
+ * *tflops.  Synchronises; allocates no device memory. */
+vlbm_status vlbm_measure_fp64_peak(int32_t reps, double* tflops);
 
 /* Human-readable name of a status code (static storage). */
 const char* vlbm_status_string(vlbm_status s);

@@ -48,7 +48,16 @@ struct vlbm_s {
   bool last_step_pulled = true;
   long long n_host = 0;        // steps completed, as of the last synchronisation
   static constexpr int kChunk = 32;
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  // Graph chunks of kChunk steps: graph[0], graph[1] start on buffer 0 / 1; graph[2] is the first
+  // chunk after vlbm_init (its first step reads the equilibrium populations in place).  pgraph:
+  // the same chunks with an event-record node before and after every step-kernel launch
+  // (profiling), whose events are gev[which][2j], gev[which][2j + 1] for step j of the chunk.
+  cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
+  cudaGraphExec_t pgraph[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t gev[3][2 * kChunk] = {};
+  int gev_pending = -1;       // event set of the last profiled chunk launch, not yet read
+  double prof_ms = 0.0;       // summed step-kernel time of the profiled chunks read so far
+  long long prof_n = 0;       // their step-kernel launches
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // adjoint workspace (allocated on first use, grown when needed)
   struct Adj {
@@ -114,11 +123,16 @@ bool is_device_ptr(const void* ptr) {
 }
 
 void destroy_graphs(vlbm_t h) {
-  for (int j = 0; j < 2; ++j)
+  for (int j = 0; j < 3; ++j) {
     if (h->graph[j]) {
       cudaGraphExecDestroy(h->graph[j]);
       h->graph[j] = nullptr;
     }
+    if (h->pgraph[j]) {
+      cudaGraphExecDestroy(h->pgraph[j]);
+      h->pgraph[j] = nullptr;
+    }
+  }
 }
 
 // Next pair of profiling events (grows the pool).
@@ -135,8 +149,10 @@ cudaError_t profile_pair(vlbm_t h, cudaEvent_t* a, cudaEvent_t* b) {
   return cudaSuccess;
 }
 
-// Issues one step (reading buffer `par`) on stream s.
-cudaError_t issue_step(vlbm_t h, cudaStream_t s, int par, int pulled, bool record = false) {
+// Issues one step (reading buffer `par`) on stream s.  With events ea, eb the step-kernel launch
+// is bracketed by them (recorded as event-record nodes when s is being captured).
+cudaError_t issue_step(vlbm_t h, cudaStream_t s, int par, int pulled, cudaEvent_t ea = nullptr,
+                       cudaEvent_t eb = nullptr, bool capturing = false) {
   vlbm::Launch L = launch_of(h, s);
   const void* fin = h->buf[par];
   void* fout = h->buf[par ^ 1];
@@ -147,33 +163,96 @@ cudaError_t issue_step(vlbm_t h, cudaStream_t s, int par, int pulled, bool recor
   }
   e = vlbm::launch_dt(L);
   if (e != cudaSuccess) return e;
-  cudaEvent_t ea = nullptr, eb = nullptr;
-  if (record) {
-    e = profile_pair(h, &ea, &eb);
-    if (e != cudaSuccess) return e;
-    e = cudaEventRecord(ea, s);
+  const unsigned flags = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+  if (ea) {
+    e = cudaEventRecordWithFlags(ea, s, flags);
     if (e != cudaSuccess) return e;
   }
   e = vlbm::launch_step(L, h->precision, h->lookahead, fin, fout, pulled);
-  if (e != cudaSuccess || !record) return e;
-  return cudaEventRecord(eb, s);
+  if (e != cudaSuccess || !eb) return e;
+  return cudaEventRecordWithFlags(eb, s, flags);
 }
 
-cudaError_t build_graph(vlbm_t h, int par) {
+// One step issued on its own (outside a graph chunk), bracketed by a pool event pair when
+// profiling.
+cudaError_t issue_single(vlbm_t h, int par, int pulled) {
+  cudaEvent_t ea = nullptr, eb = nullptr;
+  if (h->profile) {
+    cudaError_t e = profile_pair(h, &ea, &eb);
+    if (e != cudaSuccess) return e;
+  }
+  return issue_step(h, h->stream, par, pulled, ea, eb, false);
+}
+
+// Captures graph chunk `which` (0, 1: kChunk pulled steps starting on buffer 0 / 1; 2: the first
+// chunk after vlbm_init, starting on buffer 0 with the in-place step), with event-record nodes
+// around the step kernels when `prof`.
+cudaError_t build_graph(vlbm_t h, int which, bool prof) {
+  if (prof)
+    for (int j = 0; j < 2 * vlbm_s::kChunk; ++j)
+      if (!h->gev[which][j]) {
+        cudaError_t e = cudaEventCreate(&h->gev[which][j]);
+        if (e != cudaSuccess) return e;
+      }
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return e;
   cudaError_t le = cudaSuccess;
-  for (int j = 0; j < vlbm_s::kChunk && le == cudaSuccess; ++j) le = issue_step(h, h->cap_stream, par ^ (j & 1), 1);
+  for (int j = 0; j < vlbm_s::kChunk && le == cudaSuccess; ++j) {
+    const int par = which == 2 ? (j & 1) : which ^ (j & 1);
+    const int pulled = (which == 2 && j == 0) ? 0 : 1;
+    cudaEvent_t ea = prof ? h->gev[which][2 * j] : nullptr, eb = prof ? h->gev[which][2 * j + 1] : nullptr;
+    le = issue_step(h, h->cap_stream, par, pulled, ea, eb, true);
+  }
   e = cudaStreamEndCapture(h->cap_stream, &g);
   if (le != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
     return le;
   }
   if (e != cudaSuccess) return e;
-  e = cudaGraphInstantiate(&h->graph[par], g, 0);
+  e = cudaGraphInstantiate(prof ? &h->pgraph[which] : &h->graph[which], g, 0);
   cudaGraphDestroy(g);
   return e;
+}
+
+// Reads the step-kernel times of the last profiled chunk (the stream must have drained).
+cudaError_t harvest_chunk_events(vlbm_t h) {
+  if (h->gev_pending < 0) return cudaSuccess;
+  const int w = h->gev_pending;
+  h->gev_pending = -1;
+  for (int j = 0; j < vlbm_s::kChunk; ++j) {
+    float ms = 0.f;
+    cudaError_t e = cudaEventElapsedTime(&ms, h->gev[w][2 * j], h->gev[w][2 * j + 1]);
+    if (e != cudaSuccess) return e;
+    h->prof_ms += ms;
+  }
+  h->prof_n += vlbm_s::kChunk;
+  return cudaSuccess;
+}
+
+// Launches graph chunk `which` on the caller's stream (captured on first use).  When profiling,
+// a chunk whose events have not been read yet is read first (one host synchronisation; a
+// vlbm_step call of at most one chunk never needs it, its events are read at the call's end).
+cudaError_t launch_chunk(vlbm_t h, int which) {
+  if (h->profile) {
+    if (h->gev_pending >= 0) {
+      cudaError_t e = cudaStreamSynchronize(h->stream);
+      if (e == cudaSuccess) e = harvest_chunk_events(h);
+      if (e != cudaSuccess) return e;
+    }
+    if (!h->pgraph[which]) {
+      cudaError_t e = build_graph(h, which, true);
+      if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = cudaGraphLaunch(h->pgraph[which], h->stream);
+    if (e == cudaSuccess) h->gev_pending = which;
+    return e;
+  }
+  if (!h->graph[which]) {
+    cudaError_t e = build_graph(h, which, false);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaGraphLaunch(h->graph[which], h->stream);
 }
 
 // Grows the history arrays to hold at least `need` steps (keeps the recorded part).
@@ -216,12 +295,6 @@ vlbm_status sync_scalars(vlbm_t h) {
 
 bool valid_params(const vlbm_params* q) {
   if (!(q->cfl > 0.0 && q->cfl < 1.0)) return false;
-  if (q->beta_mode != VLBM_BETA_SENSOR && q->beta_mode != VLBM_BETA_CONST) return false;
-  if (q->beta_mode == VLBM_BETA_CONST && !(q->beta_const > 0.0 && q->beta_const <= 1.0)) return false;
-  if (q->beta_mode == VLBM_BETA_SENSOR) {
-    if (!(q->beta_min > 0.0 && q->beta_min <= q->beta_max && q->beta_max <= 1.0)) return false;
-    if (!(q->c_sensor >= 0.0) || !(q->ducros_eps > 0.0)) return false;
-  }
   if (q->retarget_every < 1) return false;
   if (q->precision != VLBM_FP64 && q->precision != VLBM_FP32_STORE) return false;
   if (q->algorithm < VLBM_ALGO_AUTO || q->algorithm > VLBM_ALGO_LOOKAHEAD) return false;
@@ -231,53 +304,35 @@ bool valid_params(const vlbm_params* q) {
 
 }  // namespace
 
-extern "C" {
+namespace vlbm {
 
-const char* vlbm_status_string(vlbm_status s) {
-  switch (s) {
-    case VLBM_OK: return "ok";
-    case VLBM_E_INVAL: return "invalid argument";
-    case VLBM_E_NOMEM: return "out of memory";
-    case VLBM_E_CUDA: return "CUDA error";
-    case VLBM_E_NONPHYSICAL: return "non-physical state (rho <= 0, c_s^2 <= 0 or non-finite)";
-    case VLBM_E_TIMEOUT: return "timeout";
-    case VLBM_E_STATE: return "call out of order";
-    case VLBM_E_CHECKSUM: return "checksum mismatch";
-    case VLBM_E_UNSUPPORTED: return "unsupported combination";
+bool valid_problem(const vlbm_grid* grid, const vlbm_eos* eos, const vlbm_params* q) {
+  if (grid->dim != 1 && grid->dim != 2) return false;
+  const long long nx = grid->nx, ny = grid->dim == 1 ? 1 : grid->ny;
+  if (nx < 1 || ny < 1) return false;
+  if (!(grid->x1 > grid->x0)) return false;
+  for (int j = 0; j < 4; ++j)
+    if (grid->bc[j] != VLBM_BC_PERIODIC && grid->bc[j] != VLBM_BC_ZEROGRAD) return false;
+  if ((grid->bc[0] == VLBM_BC_PERIODIC) != (grid->bc[1] == VLBM_BC_PERIODIC)) return false;
+  if (grid->dim == 2 && (grid->bc[2] == VLBM_BC_PERIODIC) != (grid->bc[3] == VLBM_BC_PERIODIC)) return false;
+  if (eos->kind == VLBM_EOS_IDEAL) {
+    if (!(eos->gamma > 1.0)) return false;
+  } else if (eos->kind == VLBM_EOS_VDW) {
+    if (!(eos->a >= 0.0 && eos->b >= 0.0 && eos->R > 0.0 && eos->cv > 0.0)) return false;
+  } else {
+    return false;
   }
-  return "unknown status";
+  if (q->beta_mode != VLBM_BETA_SENSOR && q->beta_mode != VLBM_BETA_CONST) return false;
+  if (q->beta_mode == VLBM_BETA_CONST && !(q->beta_const > 0.0 && q->beta_const <= 1.0)) return false;
+  if (q->beta_mode == VLBM_BETA_SENSOR) {
+    if (!(q->beta_min > 0.0 && q->beta_min <= q->beta_max && q->beta_max <= 1.0)) return false;
+    if (!(q->c_sensor >= 0.0) || !(q->ducros_eps > 0.0)) return false;
+  }
+  return true;
 }
 
-const char* vlbm_version(void) { return "vlbm-b300 0.1 (sm_103a)"; }
-
-vlbm_status vlbm_create(const vlbm_grid* grid, const vlbm_eos* eos, const vlbm_params* params, void* cuda_stream,
-                        vlbm_t* out) {
-  if (out) *out = nullptr;
-  if (!grid || !eos || !params || !out) return VLBM_E_INVAL;
-  if (grid->dim != 1 && grid->dim != 2) return VLBM_E_INVAL;
+void make_kparams(const vlbm_grid* grid, const vlbm_eos* eos, const vlbm_params* params, KParams& p) {
   const long long nx = grid->nx, ny = grid->dim == 1 ? 1 : grid->ny;
-  // 32-bit population offsets: 2D * 4 * nx * ny values per buffer must stay below 2^31
-  const long long nvals = 2LL * grid->dim * 4;
-  if (nx < 1 || ny < 1 || nx > 2147483647LL || ny > 2147483647LL || nx * ny > 2147483647LL / nvals) return VLBM_E_INVAL;
-  if (!(grid->x1 > grid->x0)) return VLBM_E_INVAL;
-  for (int j = 0; j < 4; ++j)
-    if (grid->bc[j] != VLBM_BC_PERIODIC && grid->bc[j] != VLBM_BC_ZEROGRAD) return VLBM_E_INVAL;
-  if ((grid->bc[0] == VLBM_BC_PERIODIC) != (grid->bc[1] == VLBM_BC_PERIODIC)) return VLBM_E_INVAL;
-  if (grid->dim == 2 && (grid->bc[2] == VLBM_BC_PERIODIC) != (grid->bc[3] == VLBM_BC_PERIODIC)) return VLBM_E_INVAL;
-  if (eos->kind == VLBM_EOS_IDEAL) {
-    if (!(eos->gamma > 1.0)) return VLBM_E_INVAL;
-  } else if (eos->kind == VLBM_EOS_VDW) {
-    if (!(eos->a >= 0.0 && eos->b >= 0.0 && eos->R > 0.0 && eos->cv > 0.0)) return VLBM_E_INVAL;
-  } else {
-    return VLBM_E_INVAL;
-  }
-  if (!valid_params(params)) return VLBM_E_INVAL;
-
-  vlbm_s* h = new (std::nothrow) vlbm_s();
-  if (!h) return VLBM_E_NOMEM;
-  cudaGetDevice(&h->device);
-  h->stream = (cudaStream_t)cuda_stream;
-  KParams& p = h->p;
   p.dim = grid->dim;
   p.nc = grid->dim + 2;
   p.q = 2 * grid->dim;
@@ -307,41 +362,78 @@ vlbm_status vlbm_create(const vlbm_grid* grid, const vlbm_eos* eos, const vlbm_p
   // (per step, 1 GPU): FP64 strips 8.0 ms vs tiles 8.9 ms; FP32 storage strips 0.59 ms
   // (look-ahead) vs tiles 0.73 ms (two-pass).
   p.strip = (grid->dim == 2 && params->tiling != VLBM_TILING_TILE) ? 1 : 0;
-  p.max_parts = vlbm::max_partials(p);
-  {
-    vlbm::Coef<double>& c = p.cd;
-    c.gamma = p.gamma;
-    c.gm1 = p.gamma - 1.0;
-    c.ggm1 = p.gamma * (p.gamma - 1.0);
-    c.a = p.a;
-    c.b = p.b;
-    c.R = p.R;
-    c.inv_cv = p.inv_cv;
-    c.a_inv_cv = p.a * p.inv_cv;
-    c.c_sensor = p.c_sensor;
-    c.beta_max = p.beta_max;
-    c.dbeta = p.beta_max - p.beta_min;
-    c.beta_const = p.beta_const;
-    c.eps_lat = p.ducros_eps * (2.0 * p.dx) * (2.0 * p.dx);
-    c.c_chi2 = p.c_sensor / 512.0;
-    c.c_chi1 = p.c_sensor / (4.0 * std::sqrt(3.0));
-    vlbm::Coef<float>& f = p.cf;
-    f.gamma = (float)c.gamma;
-    f.gm1 = (float)c.gm1;
-    f.ggm1 = (float)c.ggm1;
-    f.a = (float)c.a;
-    f.b = (float)c.b;
-    f.R = (float)c.R;
-    f.inv_cv = (float)c.inv_cv;
-    f.a_inv_cv = (float)c.a_inv_cv;
-    f.c_sensor = (float)c.c_sensor;
-    f.beta_max = (float)c.beta_max;
-    f.dbeta = (float)c.dbeta;
-    f.beta_const = (float)c.beta_const;
-    f.eps_lat = (float)c.eps_lat;
-    f.c_chi2 = (float)c.c_chi2;
-    f.c_chi1 = (float)c.c_chi1;
+  Coef<double>& c = p.cd;
+  c.gamma = p.gamma;
+  c.gm1 = p.gamma - 1.0;
+  c.ggm1 = p.gamma * (p.gamma - 1.0);
+  c.a = p.a;
+  c.b = p.b;
+  c.R = p.R;
+  c.inv_cv = p.inv_cv;
+  c.a_inv_cv = p.a * p.inv_cv;
+  c.c_sensor = p.c_sensor;
+  c.beta_max = p.beta_max;
+  c.dbeta = p.beta_max - p.beta_min;
+  c.beta_const = p.beta_const;
+  c.eps_lat = p.ducros_eps * (2.0 * p.dx) * (2.0 * p.dx);
+  c.c_chi2 = p.c_sensor / 512.0;
+  c.c_chi1 = p.c_sensor / (4.0 * std::sqrt(3.0));
+  Coef<float>& f = p.cf;
+  f.gamma = (float)c.gamma;
+  f.gm1 = (float)c.gm1;
+  f.ggm1 = (float)c.ggm1;
+  f.a = (float)c.a;
+  f.b = (float)c.b;
+  f.R = (float)c.R;
+  f.inv_cv = (float)c.inv_cv;
+  f.a_inv_cv = (float)c.a_inv_cv;
+  f.c_sensor = (float)c.c_sensor;
+  f.beta_max = (float)c.beta_max;
+  f.dbeta = (float)c.dbeta;
+  f.beta_const = (float)c.beta_const;
+  f.eps_lat = (float)c.eps_lat;
+  f.c_chi2 = (float)c.c_chi2;
+  f.c_chi1 = (float)c.c_chi1;
+}
+
+}  // namespace vlbm
+
+extern "C" {
+
+const char* vlbm_status_string(vlbm_status s) {
+  switch (s) {
+    case VLBM_OK: return "ok";
+    case VLBM_E_INVAL: return "invalid argument";
+    case VLBM_E_NOMEM: return "out of memory";
+    case VLBM_E_CUDA: return "CUDA error";
+    case VLBM_E_NONPHYSICAL: return "non-physical state (rho <= 0, c_s^2 <= 0 or non-finite)";
+    case VLBM_E_TIMEOUT: return "timeout";
+    case VLBM_E_STATE: return "call out of order";
+    case VLBM_E_CHECKSUM: return "checksum mismatch";
+    case VLBM_E_UNSUPPORTED: return "unsupported combination";
   }
+  return "unknown status";
+}
+
+const char* vlbm_version(void) { return "vlbm-b300 0.1 (sm_103a)"; }
+
+vlbm_status vlbm_create(const vlbm_grid* grid, const vlbm_eos* eos, const vlbm_params* params, void* cuda_stream,
+                        vlbm_t* out) {
+  if (out) *out = nullptr;
+  if (!grid || !eos || !params || !out) return VLBM_E_INVAL;
+  if (!vlbm::valid_problem(grid, eos, params) || !valid_params(params)) return VLBM_E_INVAL;
+  const long long nx = grid->nx, ny = grid->dim == 1 ? 1 : grid->ny;
+  // 32-bit population offsets: 2D * 4 * nx * ny values per buffer must stay below 2^31
+  const long long nvals = 2LL * grid->dim * 4;
+  if (nx > 2147483647LL || ny > 2147483647LL || nx * ny > 2147483647LL / nvals) return VLBM_E_INVAL;
+
+  vlbm_s* h = new (std::nothrow) vlbm_s();
+  if (!h) return VLBM_E_NOMEM;
+  cudaGetDevice(&h->device);
+  h->stream = (cudaStream_t)cuda_stream;
+  KParams& p = h->p;
+  vlbm::make_kparams(grid, eos, params, p);
+  p.max_parts = vlbm::max_partials(p);
   h->precision = params->precision;
   h->elem = params->precision == VLBM_FP64 ? 8 : 4;
   // Look-ahead (one pass over HBM per step) for FP32 storage, which is bandwidth-bound: 0.59 vs
@@ -419,6 +511,9 @@ vlbm_status vlbm_destroy(vlbm_t h) {
   cudaFree(h->adj.sc_backup);
   if (h->adj.as_host) cudaFreeHost(h->adj.as_host);
   for (cudaEvent_t e : h->pev) cudaEventDestroy(e);
+  for (auto& set : h->gev)
+    for (cudaEvent_t e : set)
+      if (e) cudaEventDestroy(e);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -478,33 +573,29 @@ vlbm_status vlbm_step(vlbm_t h, int64_t n_steps, double t_end, int64_t* steps_do
     st = ensure_history(h, n_expect + vlbm_s::kChunk + 1);
     if (st != VLBM_OK) break;
     const int par = (int)(n_expect & 1);
-    if (h->unpulled) {  // first step after vlbm_init reads the equilibrium in place
-      VLBM_TRY(issue_step(h, h->stream, par, 0, h->profile));
-      h->unpulled = false;
-      h->last_step_pulled = false;
-      ++issued;
-      ++n_expect;
-      continue;
-    }
-    if (n_steps - issued >= vlbm_s::kChunk && !h->profile) {
-      if (!h->graph[par]) VLBM_TRY(build_graph(h, par));
-      VLBM_TRY(cudaGraphLaunch(h->graph[par], h->stream));
+    const bool first = h->unpulled;  // first step after vlbm_init reads the equilibrium in place
+    if (n_steps - issued >= vlbm_s::kChunk) {
+      VLBM_TRY(launch_chunk(h, first ? 2 : par));
       issued += vlbm_s::kChunk;
       n_expect += vlbm_s::kChunk;
+      h->last_step_pulled = true;
     } else {
-      VLBM_TRY(issue_step(h, h->stream, par, 1, h->profile));
+      VLBM_TRY(issue_single(h, par, first ? 0 : 1));
       ++issued;
       ++n_expect;
+      h->last_step_pulled = !first;
     }
-    h->last_step_pulled = true;
+    h->unpulled = false;
     if (poll && issued < n_steps) {
       st = sync_scalars(h);
+      if (st == VLBM_OK) st = cuda_status(harvest_chunk_events(h));
       if (st != VLBM_OK) break;
       if (h->sc_host->done) break;
       n_expect = h->n_host;
     }
   }
   vlbm_status st2 = sync_scalars(h);
+  if (st2 == VLBM_OK) st2 = cuda_status(harvest_chunk_events(h));
   if (steps_done) *steps_done = h->n_host - n0;
   if (h->n_host == n0 + 1 && n0 == 0) h->last_step_pulled = false;
   if (st != VLBM_OK) return st;
@@ -746,21 +837,27 @@ vlbm_status vlbm_set_profiling(vlbm_t h, int32_t on) {
   VLBM_TRY(cudaStreamSynchronize(h->stream));
   h->profile = on != 0;
   h->pev_used = 0;
+  h->gev_pending = -1;
+  h->prof_ms = 0.0;
+  h->prof_n = 0;
   return VLBM_OK;
 }
 
 vlbm_status vlbm_get_profile(vlbm_t h, double* ms_total, int64_t* launches) {
   if (!h) return VLBM_E_INVAL;
   VLBM_TRY(cudaStreamSynchronize(h->stream));
-  double tot = 0.0;
+  VLBM_TRY(harvest_chunk_events(h));
+  double tot = h->prof_ms;
   for (size_t j = 0; j + 1 < h->pev_used; j += 2) {
     float ms = 0.f;
     VLBM_TRY(cudaEventElapsedTime(&ms, h->pev[j], h->pev[j + 1]));
     tot += ms;
   }
   if (ms_total) *ms_total = tot;
-  if (launches) *launches = (int64_t)(h->pev_used / 2);
+  if (launches) *launches = (int64_t)(h->pev_used / 2) + h->prof_n;
   h->pev_used = 0;
+  h->prof_ms = 0.0;
+  h->prof_n = 0;
   return VLBM_OK;
 }
 

@@ -4,6 +4,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "vlbm.h"
+
 namespace vlbm {
 
 // Device-resident scalars of one solver.  Written only by the one-thread link-speed kernel
@@ -72,6 +74,14 @@ struct KParams {
   Coef<double> cd;
   Coef<float> cf;
 };
+
+// Problem set-up shared by vlbm_create and vlbm_beta_noalloc (defined in vlbm_capi.cu).
+// valid_problem checks the grid's dimension, extent and boundary pairing, the EOS parameters and
+// the sensor fields of the parameters (not the sizes: each entry point has its own limit);
+// make_kparams fills the per-solver parameters and the precomputed coefficients of both
+// arithmetic types.
+bool valid_problem(const vlbm_grid* grid, const vlbm_eos* eos, const vlbm_params* params);
+void make_kparams(const vlbm_grid* grid, const vlbm_eos* eos, const vlbm_params* params, KParams& p);
 
 // Host-side launch helpers (defined in vlbm_kernels.cu).
 struct Launch {

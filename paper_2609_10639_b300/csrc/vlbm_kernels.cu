@@ -31,9 +31,11 @@
 #include "vlbm_device.cuh"
 #include "vlbm_internal.cuh"
 
+#include <atomic>
 #include <cfloat>
 #include <cstddef>
 #include <cmath>
+#include <mutex>
 #include <type_traits>
 
 namespace vlbm {
@@ -820,7 +822,8 @@ static_assert(sizeof(Scalars) <= kNoallocScalarsBytes, "scalar block does not fi
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 
 constexpr int kNoallocMaxDevices = 64;
-unsigned char* g_noalloc_addr[kNoallocMaxDevices] = {nullptr};  // device address, per device ordinal
+std::atomic<unsigned char*> g_noalloc_addr[kNoallocMaxDevices];  // device address, per device ordinal
+std::mutex g_noalloc_mutex;                                        // serialises the first-call set-up
 }  // namespace
 
 }  // namespace vlbm
@@ -829,90 +832,42 @@ extern "C" vlbm_status vlbm_beta_noalloc(const vlbm_grid* grid, const vlbm_eos* 
                                          const double* f, int32_t in_place, double* beta, void* cuda_stream) {
   using namespace vlbm;
   if (!grid || !eos || !params || !f || !beta) return VLBM_E_INVAL;
-  if (grid->dim != 1 && grid->dim != 2) return VLBM_E_INVAL;
+  if (!valid_problem(grid, eos, params)) return VLBM_E_INVAL;
+  // beyond the fixed scratch: rejected (each axis first, so that nx * ny cannot overflow)
   const long long nx = grid->nx, ny = grid->dim == 1 ? 1 : grid->ny;
-  if (nx < 1 || ny < 1) return VLBM_E_INVAL;
-  if (nx * ny > kNoallocMaxCells) return VLBM_E_INVAL;  // beyond the fixed scratch: rejected
-  for (int j = 0; j < 4; ++j)
-    if (grid->bc[j] != VLBM_BC_PERIODIC && grid->bc[j] != VLBM_BC_ZEROGRAD) return VLBM_E_INVAL;
-  if ((grid->bc[0] == VLBM_BC_PERIODIC) != (grid->bc[1] == VLBM_BC_PERIODIC)) return VLBM_E_INVAL;
-  if (grid->dim == 2 && (grid->bc[2] == VLBM_BC_PERIODIC) != (grid->bc[3] == VLBM_BC_PERIODIC)) return VLBM_E_INVAL;
-  if (!(grid->x1 > grid->x0)) return VLBM_E_INVAL;
-  if (eos->kind == VLBM_EOS_IDEAL ? !(eos->gamma > 1.0)
-                                  : (eos->kind != VLBM_EOS_VDW || !(eos->a >= 0.0 && eos->b >= 0.0 && eos->R > 0.0 && eos->cv > 0.0)))
-    return VLBM_E_INVAL;
-  if (params->beta_mode != VLBM_BETA_SENSOR && params->beta_mode != VLBM_BETA_CONST) return VLBM_E_INVAL;
-  if (params->beta_mode == VLBM_BETA_SENSOR &&
-      !(params->beta_min > 0.0 && params->beta_min <= params->beta_max && params->beta_max <= 1.0 &&
-        params->c_sensor >= 0.0 && params->ducros_eps > 0.0))
-    return VLBM_E_INVAL;
-  if (params->beta_mode == VLBM_BETA_CONST && !(params->beta_const > 0.0 && params->beta_const <= 1.0))
-    return VLBM_E_INVAL;
+  if (nx > kNoallocMaxCells || ny > kNoallocMaxCells || nx * ny > kNoallocMaxCells) return VLBM_E_INVAL;
 
-  // Set-up, once per device, with that device current: the device address of the static array.
+  // Set-up, once per device, with that device current: the device address of the static array
+  // and the kernels' shared-memory attribute.  Guarded, so that host threads making their first
+  // calls at the same time set it up once.
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoallocMaxDevices) return VLBM_E_CUDA;
-  if (!g_noalloc_addr[dev]) {
-    void* ptr = nullptr;
-    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return VLBM_E_CUDA;
-    if (cudaFuncSetAttribute(k_tile<1, double, false, true, TileCfg<1>::TX, TileCfg<1>::TY>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)TileGeom<1, double, false, TileCfg<1>::TX, TileCfg<1>::TY>::smem_bytes) != cudaSuccess ||
-        cudaFuncSetAttribute(k_tile<2, double, false, true, TileCfg<2>::TX, TileCfg<2>::TY>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)TileGeom<2, double, false, TileCfg<2>::TX, TileCfg<2>::TY>::smem_bytes) != cudaSuccess)
-      return VLBM_E_CUDA;
-    g_noalloc_addr[dev] = static_cast<unsigned char*>(ptr);
+  unsigned char* base = g_noalloc_addr[dev].load(std::memory_order_acquire);
+  if (!base) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    base = g_noalloc_addr[dev].load(std::memory_order_relaxed);
+    if (!base) {
+      void* ptr = nullptr;
+      if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return VLBM_E_CUDA;
+      if (cudaFuncSetAttribute(k_tile<1, double, false, true, TileCfg<1>::TX, TileCfg<1>::TY>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)TileGeom<1, double, false, TileCfg<1>::TX, TileCfg<1>::TY>::smem_bytes) != cudaSuccess ||
+          cudaFuncSetAttribute(k_tile<2, double, false, true, TileCfg<2>::TX, TileCfg<2>::TY>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)TileGeom<2, double, false, TileCfg<2>::TX, TileCfg<2>::TY>::smem_bytes) != cudaSuccess)
+        return VLBM_E_CUDA;
+      base = static_cast<unsigned char*>(ptr);
+      g_noalloc_addr[dev].store(base, std::memory_order_release);
+    }
   }
-  unsigned char* base = g_noalloc_addr[dev];
   Scalars* sc = reinterpret_cast<Scalars*>(base);
   double* invM = reinterpret_cast<double*>(base + kNoallocScalarsBytes);
   double* part = reinterpret_cast<double*>(base + kNoallocScalarsBytes + kNoallocInvMBytes);
 
   KParams p{};
-  p.dim = grid->dim;
-  p.nc = grid->dim + 2;
-  p.q = 2 * grid->dim;
-  p.nx = (int)nx;
-  p.ny = (int)ny;
-  p.plane = nx * ny;
-  for (int j = 0; j < 4; ++j) p.bc[j] = grid->bc[j];
-  if (grid->dim == 1) p.bc[2] = p.bc[3] = VLBM_BC_ZEROGRAD;
-  p.dx = (grid->x1 - grid->x0) / (double)nx;
-  p.inv2dx = 1.0 / (2.0 * p.dx);
-  p.eos_kind = eos->kind;
-  p.gamma = eos->kind == VLBM_EOS_IDEAL ? eos->gamma : 1.0 + eos->R / eos->cv;
-  p.a = eos->a;
-  p.b = eos->b;
-  p.R = eos->R;
-  p.cv = eos->cv;
-  p.inv_cv = eos->kind == VLBM_EOS_VDW ? 1.0 / eos->cv : 0.0;
-  p.cfl = 0.5;
-  p.beta_mode = params->beta_mode;
-  p.beta_const = params->beta_const;
-  p.beta_min = params->beta_min;
-  p.beta_max = params->beta_max;
-  p.c_sensor = params->c_sensor;
-  p.ducros_eps = params->ducros_eps;
-  p.retarget_every = 1;
+  make_kparams(grid, eos, params, p);  // the same parameters and coefficients as vlbm_create
   const int ncta = (int)((p.plane + kNoallocCtaCells - 1) / kNoallocCtaCells);
   p.max_parts = ncta;
-  Coef<double>& c = p.cd;
-  c.gamma = p.gamma;
-  c.gm1 = p.gamma - 1.0;
-  c.ggm1 = p.gamma * (p.gamma - 1.0);
-  c.a = p.a;
-  c.b = p.b;
-  c.R = p.R;
-  c.inv_cv = p.inv_cv;
-  c.a_inv_cv = p.a * p.inv_cv;
-  c.c_sensor = p.c_sensor;
-  c.beta_max = p.beta_max;
-  c.dbeta = p.beta_max - p.beta_min;
-  c.beta_const = p.beta_const;
-  c.eps_lat = p.ducros_eps * (2.0 * p.dx) * (2.0 * p.dx);
-  c.c_chi2 = p.c_sensor / 512.0;
-  c.c_chi1 = p.c_sensor / (4.0 * sqrt(3.0));
 
   cudaStream_t s = (cudaStream_t)cuda_stream;
   const int pulled = in_place ? 0 : 1;
@@ -936,3 +891,61 @@ extern "C" vlbm_status vlbm_beta_noalloc(const vlbm_grid* grid, const vlbm_eos* 
   return cudaGetLastError() == cudaSuccess ? VLBM_OK : VLBM_E_CUDA;
 }
 
+
+// ==========================================================================================
+// FP64 throughput of this GPU (the denominator of the FP64 path's ALU roofline): every thread
+// runs eight independent chains of dependent FP64 fused multiply-adds, the grid fills every SM.
+// ==========================================================================================
+namespace vlbm {
+namespace {
+__device__ double g_fma_sink;
+
+constexpr int kFmaThreads = 256, kFmaChains = 8;
+
+__global__ void __launch_bounds__(kFmaThreads) k_dfma_rate(double m, double c, int iters, int write) {
+  double a[kFmaChains];
+#pragma unroll
+  for (int j = 0; j < kFmaChains; ++j) a[j] = 1.0 + 1e-3 * (threadIdx.x + j);
+  for (int it = 0; it < iters; ++it)
+#pragma unroll
+    for (int j = 0; j < kFmaChains; ++j) a[j] = fma(a[j], m, c);
+  double sum = 0.0;
+#pragma unroll
+  for (int j = 0; j < kFmaChains; ++j) sum += a[j];
+  if (write) g_fma_sink = sum;  // never taken at run time; keeps the chains live
+}
+}  // namespace
+}  // namespace vlbm
+
+extern "C" vlbm_status vlbm_measure_fp64_peak(int32_t reps, double* tflops) {
+  using namespace vlbm;
+  if (reps < 1 || !tflops) return VLBM_E_INVAL;
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dfma_rate, kFmaThreads, 0) != cudaSuccess || per_sm < 1)
+    return VLBM_E_CUDA;
+  const int grid = sms * per_sm, iters = 8192;
+  cudaStream_t s = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  vlbm_status st = VLBM_OK;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+      cudaEventCreate(&e1) != cudaSuccess)
+    st = VLBM_E_CUDA;
+  double best = 0.0;
+  k_dfma_rate<<<grid, kFmaThreads, 0, s>>>(0.9999999, 1e-7, iters, 0);  // warm-up
+  for (int r = 0; r < reps && st == VLBM_OK; ++r) {
+    float ms = 0.f;
+    if (cudaEventRecord(e0, s) != cudaSuccess) st = VLBM_E_CUDA;
+    k_dfma_rate<<<grid, kFmaThreads, 0, s>>>(0.9999999, 1e-7, iters, 0);
+    if (st == VLBM_OK && (cudaGetLastError() != cudaSuccess || cudaEventRecord(e1, s) != cudaSuccess ||
+                          cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+      st = VLBM_E_CUDA;
+    const double flops = 2.0 * (double)grid * kFmaThreads * kFmaChains * iters;
+    if (st == VLBM_OK && ms > 0.f) best = flops / (ms * 1e-3) / 1e12 > best ? flops / (ms * 1e-3) / 1e12 : best;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (s) cudaStreamDestroy(s);
+  *tflops = best;
+  return st;
+}

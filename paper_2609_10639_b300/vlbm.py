@@ -75,6 +75,7 @@ def _load():
         "vlbm_get_totals": [V, D],
         "vlbm_save_state": [V, V, C.c_size_t, C.POINTER(C.c_size_t)],
         "vlbm_load_state": [V, V, C.c_size_t],
+        "vlbm_measure_fp64_peak": [I32, D],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -311,3 +312,10 @@ def beta_noalloc(cfg: Config, f, out, in_place: bool = True, stream=None) -> Non
     s = stream if stream is not None else torch.cuda.current_stream()
     _check(_lib.vlbm_beta_noalloc(C.byref(g), C.byref(eo), C.byref(p), C.c_void_p(_ptr(f)), 1 if in_place else 0,
                                   C.c_void_p(_ptr(out)), C.c_void_p(s.cuda_stream)), "vlbm_beta_noalloc")
+
+
+def measure_fp64_peak(reps: int = 5) -> float:
+    """Measured FP64 throughput of the current GPU in TFLOP/s (vlbm_measure_fp64_peak)."""
+    out = C.c_double(0.0)
+    _check(_lib.vlbm_measure_fp64_peak(int(reps), C.byref(out)), "vlbm_measure_fp64_peak")
+    return out.value

@@ -71,7 +71,8 @@ def test_kernel_digest_ignores_comments(tmp_path, monkeypatch):
 
     csrc = tmp_path / "paper_2609_10639_b300" / "csrc"
     csrc.mkdir(parents=True)
-    for name in ("vlbm_device.cuh", "vlbm_kernels.cu", "vlbm_roll.cu"):
+    assert "vlbm_internal.cuh" in bench.KERNEL_SOURCES  # Scalars, Coef, KParams shape the kernels
+    for name in bench.KERNEL_SOURCES:
         shutil.copy(os.path.join(ROOT, "paper_2609_10639_b300", "csrc", name), csrc / name)
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     d0 = bench.kernels_sha()
@@ -80,3 +81,17 @@ def test_kernel_digest_ignores_comments(tmp_path, monkeypatch):
     assert bench.kernels_sha() == d0
     roll.write_text(roll.read_text() + "\nstatic int unused_symbol = 1;\n")
     assert bench.kernels_sha() != d0
+
+
+def test_noalloc_rejects_oversized_grids_without_touching_the_gpu():
+    # vlbm_beta_noalloc checks each axis against its scratch limit before forming nx * ny, so axes
+    # whose product wraps around are refused on the host, before any CUDA call.
+    from paper_2609_10639_b300 import vlbm
+
+    L = vlbm.library()
+    e = vlbm._Eos(0, 1.4, 0, 0, 0, 0)
+    p = vlbm._Params(0.5, 0, 1.0, 0.75, 1.0, 4.0, 1e-6, 1, 0, 0, 0)
+    dummy = C.c_void_p(16)  # never dereferenced: the call returns before touching it
+    for nx, ny in ((2 ** 32, 2 ** 32), (2 ** 21 + 1, 1), (1, 2 ** 40), (2048, 1025)):
+        g = vlbm._Grid(2, nx, ny, 0.0, 1.0, 0.0, 1.0, (C.c_int32 * 4)(1, 1, 1, 1))
+        assert L.vlbm_beta_noalloc(C.byref(g), C.byref(e), C.byref(p), dummy, 1, dummy, None) == vlbm.E_INVAL

@@ -77,4 +77,6 @@ def test_reference_arm_line_on_rank_zero(monkeypatch):
     assert line["impl"] == "reference" and line["value"] > 0.0
     assert line["cpu_baseline"]["value"] == line["value"] and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
-    assert "4 FP64 steps" in line["cpu_baseline"]["sample"]
+    # one solver built once and warmed up; each timed step advances it by 8 time steps
+    assert "one solver" in line["cpu_baseline"]["sample"] and "1 x 8 FP64 steps" in line["cpu_baseline"]["sample"]
+    assert abs(line["ms_per_step"] * 1e-3 * line["value"] * 1e6 - 8 * 1024 * 1024) < 1e-6 * 8 * 1024 * 1024

@@ -54,6 +54,43 @@ def test_beta_noalloc_matches_handle_on_consecutive_calls(which):
         assert ref.min() < 1.0  # the sensor is active on these states
 
 
+@pytest.mark.parametrize("dim", [1, 2])
+def test_beta_noalloc_pulls_post_collision_populations(dim):
+    # in_place = 0: the caller's buffer holds post-collision populations f*, which the call pulls
+    # across the links, f_i(x) = f*_i(x - sigma_i) (Eq. 21).  On a periodic grid f* is the state
+    # rolled by +sigma_i, so the result must equal the handle's beta of the state itself.
+    import dataclasses
+
+    import torch
+
+    from paper_2609_10639_b300 import vlbm, workloads as wl
+
+    if dim == 2:
+        prob = dataclasses.replace(wl.QUADRANTS_2D.resized(200, 97), bc=wl.PER)
+        W0 = wl.quadrants_2d(prob, states=GOLD["laxliu_config12"]["states_NE_NW_SW_SE"])
+    else:
+        prob = dataclasses.replace(wl.SOD_1D.resized(600), bc=wl.PER)
+        W0 = wl.sod_1d(prob)
+    s = vlbm.Solver.for_problem(prob)
+    s.init(torch.from_numpy(W0).cuda())
+    for steps in (9, 4):  # two calls in a row, on two different states
+        s.step(steps)
+        ref = s.beta()
+        fi = s.populations()  # [i][k][y][x]
+        # sigma_i in the lattice order {x-, x+, y-, y+}: f*_i(x) = f_i(x + sigma_i)
+        rolls = [(1, 3), (-1, 3), (1, 2), (-1, 2)]
+        fstar = torch.stack([torch.roll(fi[i], shifts=rolls[i][0], dims=rolls[i][1] - 1) for i in range(s.q)])
+        f = torch.zeros((s.q, s.ny, s.nx, 4), dtype=torch.float64, device="cuda")
+        f[..., : s.nc] = fstar.permute(0, 2, 3, 1)
+        out = torch.full((s.ny, s.nx), float("nan"), dtype=torch.float64, device="cuda")
+        vlbm.beta_noalloc(s.cfg, f, out, in_place=False)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        assert np.isfinite(got).all()
+        assert np.abs(got - ref).max() <= TOL
+        assert ref.min() < 1.0
+
+
 def test_beta_noalloc_rejects_grids_beyond_its_scratch():
     import torch
 
@@ -65,3 +102,8 @@ def test_beta_noalloc_rejects_grids_beyond_its_scratch():
     with pytest.raises(vlbm.VLBMError) as ei:
         vlbm.beta_noalloc(cfg, f, out)
     assert ei.value.status == vlbm.E_INVAL
+    # axes whose product wraps around in 64-bit arithmetic are refused too
+    for nx, ny in ((2 ** 32, 2 ** 32), (2 ** 21 + 1, 1), (1, 2 ** 40)):
+        with pytest.raises(vlbm.VLBMError) as ei:
+            vlbm.beta_noalloc(vlbm.Config(dim=2, nx=nx, ny=ny), f, out)
+        assert ei.value.status == vlbm.E_INVAL
