@@ -21,7 +21,7 @@ LIB = os.path.join(HERE, "liboracle_vlbm.so")
 _lock = threading.Lock()
 _lib = None
 
-BC_CODE = {"periodic": 0, "zerograd": 1}
+BC_CODE = {"periodic": 0, "zerograd": 1, "inflow": 2}
 
 
 def build(force: bool = False) -> str:
@@ -55,6 +55,8 @@ def lib():
                 "orc_get_time": (None, [P, D, C.POINTER(C.c_long), D]),
                 "orc_get_hist": (Lg, [P, D, D, Lg]),
                 "orc_set_schedule": (None, [P, D, Lg]),
+                "orc_set_inflow": (I, [P, D]),
+                "orc_dual_set_inflow": (I, [P, D]),
                 "orc_eos_eval": (None, [D, C.c_double, C.c_double, D, D]),
                 "orc_fundamental_derivative": (C.c_double, [D, C.c_double, C.c_double]),
                 "orc_flux": (I, [I, D, D, D]),
@@ -116,7 +118,18 @@ class OracleSolver:
         params = dict(cfl=p.cfl, beta_min=p.beta_min, beta_max=p.beta_max, c_sensor=p.c_sensor,
                       ducros_eps=p.ducros_eps)
         params.update(over)
-        return cls(p.dim, p.nx, p.ny, p.dx, p.bc, p.eos, threads=threads, **params)
+        s = cls(p.dim, p.nx, p.ny, p.dx, p.bc, p.eos, threads=threads, **params)
+        if "inflow" in p.bc:
+            from paper_2609_10639_b300 import workloads as wl
+
+            s.set_inflow(wl.inflow_state(p))
+        return s
+
+    def set_inflow(self, W_in) -> None:
+        """State (D+2 conserved values) held by the ghost cells of the pinned-inflow x-lo side."""
+        w = np.ascontiguousarray(np.asarray(W_in, dtype=np.float64).reshape(-1))
+        if self.L.orc_set_inflow(self.h, _dp(w)):
+            raise ValueError("oracle set_inflow: non-physical state")
 
     def __del__(self):
         h = getattr(self, "h", None)
@@ -223,6 +236,11 @@ class DualOracleSolver:
     def set_schedule(self, c: np.ndarray) -> None:
         c = np.ascontiguousarray(c, dtype=np.float64)
         self.L.orc_dual_set_schedule(self.h, _dp(c), len(c))
+
+    def set_inflow(self, W_in) -> None:
+        w = np.ascontiguousarray(np.asarray(W_in, dtype=np.float64).reshape(-1))
+        if self.L.orc_dual_set_inflow(self.h, _dp(w)):
+            raise ValueError("dual oracle set_inflow: non-physical state")
 
     def init(self, W0: np.ndarray, dW0: np.ndarray | None) -> None:
         shape = (self.nc, self.ny, self.nx)

@@ -200,7 +200,7 @@ void reproject(int D, double c_old, double c_new, T* f) {
 // ------------------------------------------------------------------------------------------
 // Solver
 // ------------------------------------------------------------------------------------------
-enum { BC_PERIODIC = 0, BC_ZEROGRAD = 1 };
+enum { BC_PERIODIC = 0, BC_ZEROGRAD = 1, BC_INFLOW = 2 };
 enum { BETA_SENSOR = 0, BETA_CONST = 1 };
 enum { OK = 0, E_NONPHYSICAL = 4 };
 
@@ -210,7 +210,9 @@ struct Params {
 };
 
 // Index rule shared by streaming and every stencil (periodic: wrap; zero-gradient: clamp to
-// the edge cell, i.e. an edge-replicated ghost, Secs. IV B and IV E).
+// the edge cell, i.e. an edge-replicated ghost, Secs. IV B and IV E).  A pinned-inflow side
+// (Sec. IV H) is handled by the solver before this rule is reached (its ghost cells hold a fixed
+// state); the clamp below is never used for it.
 inline long nb(long j, long n, int bc_lo, int bc_hi) {
   if (j < 0) return bc_lo == BC_PERIODIC ? j + n : 0;
   if (j >= n) return bc_hi == BC_PERIODIC ? j - n : n - 1;
@@ -228,6 +230,13 @@ struct Solver {
   std::vector<T> f, fnext, W, u, P, cs2, Qf, s, th, tmp, beta;
   std::vector<T> s_raw, th_raw;  // s and theta before the filter (kept only on request)
   bool keep_raw = false;
+  // Pinned inflow on the x-lo side (Sec. IV H): every ghost cell x < 0 holds the fixed state
+  // W_in, whose velocity and flux are uin, qin; its post-collision populations are the
+  // equilibrium of W_in at the step's link speed.  s and theta of the ghost column x = -1 feed
+  // the box filter of the first column.
+  bool inflow = false;
+  T win[4], uin[2], qin[8];
+  std::vector<T> s_gh, th_gh;
   double c_prev = 0, t = 0;
   long n = 0;
   std::vector<double> hist_dt, hist_c, sched;
@@ -237,6 +246,53 @@ struct Solver {
   long fidx(int i, int k, long c) const { return ((long)(i * NC + k)) * N + c; }
   long xn(long x, int d) const { return nb(x + d, nx, bc[0], bc[1]); }
   long yn(long y, int d) const { return nb(y + d, ny, bc[2], bc[3]); }
+  bool ghost(long x) const { return inflow && x < 0; }
+  // Flux component Q_{a,k} and velocity u_a at position (x, y) after the boundary rules.
+  T Qat(int a, int k, long x, long y) const {
+    if (ghost(x)) return qin[a * NC + k];
+    return Qf[(size_t)(a * NC + k) * N + cell(xn(x, 0), yn(y, 0))];
+  }
+  T uat(int a, long x, long y) const {
+    if (ghost(x)) return uin[a];
+    return u[(size_t)a * N + cell(xn(x, 0), yn(y, 0))];
+  }
+
+  int set_inflow(const T* w) {
+    T P_, cs2_;
+    for (int k = 0; k < NC; ++k) win[k] = w[k];
+    if (primitives_and_flux(D, eos, win, uin, &P_, &cs2_, qin)) return E_NONPHYSICAL;
+    inflow = bc[0] == BC_INFLOW;
+    return OK;
+  }
+
+  // Local activity s at (x, y) (Eqs. 28-31): central differences, j_k = dx (div Q)_k,
+  // s_hat_k = j_k / M_k (taken as 0 where M_k = 0), s = sqrt(sum_k s_hat_k^2 / NC).
+  T activity(long x, long y, const T* M) const {
+    T acc = 0.0;
+    for (int k = 0; k < NC; ++k) {
+      T divq = 0.0;
+      for (int a = 0; a < D; ++a) {
+        T qp = a == 0 ? Qat(a, k, x + 1, y) : Qat(a, k, x, y + 1);
+        T qm = a == 0 ? Qat(a, k, x - 1, y) : Qat(a, k, x, y - 1);
+        divq = divq + (qp - qm) / (2.0 * dx);
+      }
+      T j = dx * divq;
+      T sh = val(M[k]) != 0.0 ? j / M[k] : T(0.0);
+      acc = acc + sh * sh;
+    }
+    return sqrt(acc / (double)NC);
+  }
+
+  // Ducros ratio at (x, y): dilatation and vorticity by central differences (Eq. 32), Eq. (33).
+  T ducros(long x, long y) const {
+    T dux_dx = (uat(0, x + 1, y) - uat(0, x - 1, y)) / (2.0 * dx);
+    T duy_dy = (uat(1, x, y + 1) - uat(1, x, y - 1)) / (2.0 * dx);
+    T duy_dx = (uat(1, x + 1, y) - uat(1, x - 1, y)) / (2.0 * dx);
+    T dux_dy = (uat(0, x, y + 1) - uat(0, x, y - 1)) / (2.0 * dx);
+    T dil = dux_dx + duy_dy;
+    T vort = duy_dx - dux_dy;
+    return dil * dil / (dil * dil + vort * vort + prm.ducros_eps);
+  }
 
   void alloc() {
     Q = 2 * D;
@@ -323,45 +379,29 @@ struct Solver {
         if (val(rowmax[(size_t)r]) > val(m)) m = rowmax[(size_t)r];
       M[k] = m;
     }
-    // Local activity s(x) (Eqs. 28-31): central differences, j_k = dx (div Q)_k,
-    // s_hat_k = j_k / M_k (taken as 0 where M_k = 0), s = sqrt(sum_k s_hat_k^2 / NC).
+    // Activity s (Eqs. 28-31) and, in 2D, the Ducros ratio theta (Eqs. 32-33) of every cell, and
+    // of the ghost column x = -1 of a pinned-inflow side (read by the filter of column 0).
 #pragma omp parallel for num_threads(nthreads) schedule(static)
     for (long y = 0; y < ny; ++y)
       for (long x = 0; x < nx; ++x) {
         long c = cell(x, y);
-        T acc = 0.0;
-        for (int k = 0; k < NC; ++k) {
-          T divq = 0.0;
-          for (int a = 0; a < D; ++a) {
-            long cp = a == 0 ? cell(xn(x, +1), y) : cell(x, yn(y, +1));
-            long cm = a == 0 ? cell(xn(x, -1), y) : cell(x, yn(y, -1));
-            const T* q = &Qf[(size_t)(a * NC + k) * N];
-            divq = divq + (q[cp] - q[cm]) / (2.0 * dx);
-          }
-          T j = dx * divq;
-          T sh = val(M[k]) != 0.0 ? j / M[k] : T(0.0);
-          acc = acc + sh * sh;
-        }
-        s[c] = sqrt(acc / (double)NC);
-        if (D == 2) {
-          // Dilatation and vorticity by central differences (Eq. 32); Ducros ratio (Eq. 33).
-          const T* ux = &u[0];
-          const T* uy = &u[(size_t)N];
-          long xp = cell(xn(x, +1), y), xm = cell(xn(x, -1), y);
-          long yp = cell(x, yn(y, +1)), ym = cell(x, yn(y, -1));
-          T dux_dx = (ux[xp] - ux[xm]) / (2.0 * dx), duy_dy = (uy[yp] - uy[ym]) / (2.0 * dx);
-          T duy_dx = (uy[xp] - uy[xm]) / (2.0 * dx), dux_dy = (ux[yp] - ux[ym]) / (2.0 * dx);
-          T dil = dux_dx + duy_dy;
-          T vort = duy_dx - dux_dy;
-          th[c] = dil * dil / (dil * dil + vort * vort + prm.ducros_eps);
-        }
+        s[c] = activity(x, y, M);
+        if (D == 2) th[c] = ducros(x, y);
       }
+    if (inflow) {
+      s_gh.assign(ny, T(0.0));
+      th_gh.assign(ny, T(0.0));
+      for (long y = 0; y < ny; ++y) {
+        s_gh[y] = activity(-1, y, M);
+        if (D == 2) th_gh[y] = ducros(-1, y);
+      }
+    }
     if (keep_raw) {
       s_raw = s;
       th_raw = th;
     }
-    box_filter(s);  // s_bar = S[s]
-    if (D == 2) box_filter(th);  // theta_bar = S[theta]
+    box_filter(s, inflow ? s_gh.data() : nullptr);  // s_bar = S[s]
+    if (D == 2) box_filter(th, inflow ? th_gh.data() : nullptr);  // theta_bar = S[theta]
     // Sensor A (1D, Eq. 34) / Sensor B (2D, Eq. 35).
 #pragma omp parallel for num_threads(nthreads) schedule(static)
     for (long c = 0; c < N; ++c) {
@@ -372,11 +412,14 @@ struct Solver {
   }
 
   // Separable one-cell box filter with weights (1/4, 1/2, 1/4), x first, then y (Sec. III D).
-  void box_filter(std::vector<T>& a) {
+  // ghost_col: the values of the ghost column x = -1 of a pinned-inflow side (else nullptr).
+  void box_filter(std::vector<T>& a, const T* ghost_col) {
 #pragma omp parallel for num_threads(nthreads) schedule(static)
     for (long y = 0; y < ny; ++y)
-      for (long x = 0; x < nx; ++x)
-        tmp[cell(x, y)] = 0.25 * a[cell(xn(x, -1), y)] + 0.5 * a[cell(x, y)] + 0.25 * a[cell(xn(x, +1), y)];
+      for (long x = 0; x < nx; ++x) {
+        T left = (ghost_col && x == 0) ? ghost_col[y] : a[cell(xn(x, -1), y)];
+        tmp[cell(x, y)] = 0.25 * left + 0.5 * a[cell(x, y)] + 0.25 * a[cell(xn(x, +1), y)];
+      }
     if (D == 1) {
       a = tmp;
       return;
@@ -439,12 +482,19 @@ struct Solver {
         }
       }
     }
-    // 8. exact transport (Eq. 21): f_i(x) <- f_i(x - sigma_i), index rule at the boundary.
+    // 8. exact transport (Eq. 21): f_i(x) <- f_i(x - sigma_i), index rule at the boundary; from a
+    // pinned-inflow ghost cell, the equilibrium of W_in at this step's link speed.
     std::vector<T>& g = fnext;
 #pragma omp parallel for num_threads(nthreads) schedule(static)
     for (long y = 0; y < ny; ++y)
       for (long x = 0; x < nx; ++x)
         for (int i = 0; i < Q; ++i) {
+          if (ghost(x - SIGMA[i][0])) {
+            T fe[4];
+            feq(D, c_new, win, qin, i, fe);
+            for (int k = 0; k < NC; ++k) g[fidx(i, k, cell(x, y))] = fe[k];
+            continue;
+          }
           long src = cell(xn(x, -SIGMA[i][0]), D == 2 ? yn(y, -SIGMA[i][1]) : y);
           for (int k = 0; k < NC; ++k) g[fidx(i, k, cell(x, y))] = f[fidx(i, k, src)];
         }
@@ -649,6 +699,14 @@ long orc_get_hist(void* h, double* dt, double* c, long cap) {
     c[j] = s->hist_c[j];
   }
   return (long)s->hist_dt.size();
+}
+// State W_in (D+2 values) held by the ghost cells of a pinned-inflow x-lo side (Sec. IV H).
+int orc_set_inflow(void* h, const double* w) { return static_cast<Solver<double>*>(h)->set_inflow(w); }
+int orc_dual_set_inflow(void* h, const double* w) {
+  auto* s = static_cast<Solver<Dual>*>(h);
+  Dual wd[4];
+  for (int k = 0; k < s->NC; ++k) wd[k] = Dual(w[k]);
+  return s->set_inflow(wd);
 }
 // Replay a fixed link-speed sequence: entry 0 is the initial link speed c0, entry j >= 1 the
 // link speed of step j-1 (a free run's history prefixed with its c0 replays that run).

@@ -55,7 +55,7 @@ class Problem:
     nx: int
     ny: int
     extent: tuple  # (x0, x1, y0, y1)
-    bc: tuple  # (x-lo, x-hi, y-lo, y-hi): "periodic" | "zerograd"
+    bc: tuple  # (x-lo, x-hi, y-lo, y-hi): "periodic" | "zerograd" | "inflow" (x-lo only, pinned state)
     eos: dict  # {"kind": "ideal", "gamma": g} | {"kind": "vdw", "a", "b", "R", "cv"}
     cfl: float
     t_end: float  # 0: run a fixed number of steps
@@ -101,8 +101,18 @@ SHU_OSHER_1D = Problem("shu_osher_1d_2000", 1, 2000, 1, (-5.0, 5.0, 0.0, 0.0), Z
 GRESHO_2D = Problem("gresho_2d_128", 2, 128, 128, (0.0, 1.0, 0.0, 1.0), PER, {"kind": "ideal", "gamma": 5.0 / 3.0}, 0.5,
                     0.5, 0)
 
+# Shock-vortex interaction (Sec. IV H): [0,16] x [0,6], stationary normal shock at x = 6 (M_s = 1.2),
+# isentropic vortex (beta_v = 2, R_c = 1) at (2, 3) in the upstream flow; left side pinned to the
+# upstream state, right side zero-gradient (outflow), y periodic.  CFL 0.5 (not stated for this case).
+INFLOW_BC = ("inflow", "zerograd", "periodic", "periodic")
+BZT_SV_EOS = {"kind": "vdw", "a": 1.0, "b": 0.3, "R": 1.0, "cv": 50.0}
+SHOCK_VORTEX_IDEAL = Problem("shock_vortex_ideal_800x300", 2, 800, 300, (0.0, 16.0, 0.0, 6.0), INFLOW_BC, IDEAL14, 0.5,
+                             7.0, 0)
+SHOCK_VORTEX_BZT = Problem("shock_vortex_bzt_1200x450", 2, 1200, 450, (0.0, 16.0, 0.0, 6.0), INFLOW_BC, BZT_SV_EOS,
+                           0.5, 15.0, 0)
+
 PROBLEMS = {p.name: p for p in (SOD_1D, QUADRANTS_2D, BZT_2D, VORTEX_SCALE_2D, VORTEX_ADJOINT_2D, STRONG_SHOCK_1D,
-                                SHU_OSHER_1D, GRESHO_2D)}
+                                SHU_OSHER_1D, GRESHO_2D, SHOCK_VORTEX_IDEAL, SHOCK_VORTEX_BZT)}
 
 
 def cell_centres(p: Problem):
@@ -400,6 +410,51 @@ def gresho_2d(p: Problem = GRESHO_2D) -> np.ndarray:
     return conserved(p.eos, rho, [u, v], P)
 
 
+_SHOCK_VORTEX_FILE = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "tests", "golden",
+                                  "shock_vortex.json")
+
+
+def shock_vortex_setup(p: Problem) -> dict:
+    """The stored set-up of the shock-vortex case whose EOS p has (written by the fixture script
+    beside the file, from the oracle's normal-shock and vortex-shooting routines): upstream and
+    downstream (rho, u, P), the vortex profile rho(r), P(r) on r = j dr, and the geometry."""
+    with open(_SHOCK_VORTEX_FILE) as fh:
+        d = json.load(fh)
+    key = "ideal" if p.eos["kind"] == "ideal" else "bzt"
+    if d[key]["eos"] != p.eos:
+        raise ValueError(f"no stored shock-vortex set-up for the EOS {p.eos}")
+    return {**d, **d[key]}
+
+
+def inflow_state(p: Problem) -> np.ndarray:
+    """Conserved state W_in held by the pinned-inflow ghost cells (the upstream shock state)."""
+    rho1, u1, P1 = shock_vortex_setup(p)["upstream"]
+    return conserved(p.eos, np.array(rho1), [np.array(u1), np.array(0.0)], np.array(P1)).reshape(-1)
+
+
+def shock_vortex_2d(p: Problem = SHOCK_VORTEX_IDEAL) -> np.ndarray:
+    """Upstream state plus the isentropic vortex for x < x_s, downstream state for x >= x_s; the
+    vortex's rho(r) and P(r) are interpolated linearly from the stored profile (ambient beyond it),
+    its velocity u_phi(r) = beta_v/(2 pi R_c) r exp((1 - r^2/R_c^2)/2) is added to (u1, 0)."""
+    d = shock_vortex_setup(p)
+    X, Y = cell_centres(p)
+    (rho1, u1, P1), (rho2, u2, P2) = d["upstream"], d["downstream"]
+    xc, yc = d["vortex_centre"]
+    bv, Rc = d["beta_v"], d["Rc"]
+    dxv, dyv = X - xc, Y - yc
+    r = np.hypot(dxv, dyv)
+    rr = np.arange(len(d["profile_rho"])) * d["profile_dr"]
+    rho_v = np.interp(r, rr, d["profile_rho"], right=rho1)
+    P_v = np.interp(r, rr, d["profile_P"], right=P1)
+    amp = bv / (2.0 * math.pi * Rc) * np.exp(0.5 * (1.0 - (r / Rc) ** 2))  # u_phi / r
+    up = X < d["x_shock"]
+    rho = np.where(up, rho_v, rho2)
+    P = np.where(up, P_v, P2)
+    u = np.where(up, u1 - amp * dyv, u2)
+    v = np.where(up, amp * dxv, 0.0)
+    return conserved(p.eos, rho, [u, v], P)
+
+
 def initial_field(p: Problem) -> np.ndarray:
     """W0 of a named problem at its (possibly resized) grid."""
     base = p.name.split("@")[0]
@@ -419,4 +474,6 @@ def initial_field(p: Problem) -> np.ndarray:
         return vortex_acoustic_2d(p)
     if base.startswith("vortex_adjoint_2d"):
         return vortex_density_2d(p)
+    if base.startswith("shock_vortex"):
+        return shock_vortex_2d(p)
     raise KeyError(p.name)
