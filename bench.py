@@ -312,6 +312,26 @@ def cpu_baselines():
     return allc
 
 
+def other_workloads(S, K, W, world):
+    """FP64 and FP32-storage throughput of the other workloads the library runs: the shock-vortex
+    interaction with its pinned-inflow boundary (ideal gas, 800 x 300) and the BZT interface input
+    with the non-polytropic gas (c_v(T), FP64 Newton inversion of e -> T; 2048^2)."""
+    import torch
+
+    from paper_2609_10639_b300 import workloads as wl
+
+    out = {}
+    for prob, make in ((wl.SHOCK_VORTEX_IDEAL, wl.shock_vortex_2d), (wl.BZT_CVT_2D, wl.bzt_interface_2d)):
+        W0 = torch.from_numpy(make(prob)).cuda()
+        entry = {"grid": [prob.nx, prob.ny]}
+        for prec in ("fp64", "fp32_store"):
+            r = time_path(prob, W0, prec, S, K, W, world)
+            entry[prec] = {"value": aggregate_mlups(world, prob.ncells, S * K, r["ms"]), "unit": UNIT,
+                           "ms_per_step": r["ms"] / K, "dominant_kernel_ms": r["kernel_ms_avg"]}
+        out[prob.name] = entry
+    return out
+
+
 def run_reference(args, n=1024, steps_per_step=8):
     """The reference arm: the oracle timed on the host cores, same metric and workload.  One oracle
     solver is built and warmed up once; each timed step advances it by `steps_per_step` time steps
@@ -397,6 +417,7 @@ def run_ours(args):
     dt_e2e, nbytes = time_e2e(prob, W0_host, "fp64", S, K, world)
     e2e64 = aggregate_mlups(world, cells, S * K, dt_e2e * 1e3)
     adj = time_adjoint(args.adjoint_steps, 32, world) if args.adjoint_steps > 0 else None
+    other = other_workloads(S, min(K, 3), Wm, world) if args.other_workloads else None
 
     if rank != 0:
         return
@@ -437,6 +458,7 @@ def run_ours(args):
                                         "kernel": "k_roll<float> (FP32-storage step kernel, column strips, look-ahead form: the whole step in one pass)",
                                         "kernel_ms": r32["kernel_ms_avg"], "peak_source": pk["source"],
                                         "bytes_per_cell": BYTES_PER_CELL["fp32_store"]}},
+            "other_workloads": other,
             "adjoint": None if adj is None else {
                 "workload": "vortex_adjoint_2d_1024 (J = sum g rho(T), checkpoints every 32 steps)",
                 "value": world * adj["cells"] * adj["steps"] / (adj["rev_ms"] * 1e-3) / 1e6, "unit": UNIT,
@@ -468,6 +490,8 @@ def main():
     ap.add_argument("--substeps", type=int, default=32)
     ap.add_argument("--adjoint-steps", type=int, default=1000, help="steps of the adjoint measurement (0: skip)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--other-workloads", type=int, default=1, help="also time the shock-vortex and non-polytropic "
+                                                                       "workloads (0: skip)")
     ap.add_argument("--only", choices=list(BYTES_PER_CELL) + ["adjoint"],
                     help="time one path only (profiling, sweeps); adjoint: the adjoint measurement alone")
     ap.add_argument("--grid", type=int, default=0, help="with --only: n x n copy of the workload")

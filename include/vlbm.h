@@ -50,8 +50,11 @@ typedef enum {
 
 /* Boundary rule per domain side (periodic pairs both sides of an axis).  Zero-gradient is the
  * edge-replicated ghost cell of Secs. IV B and IV E: every stencil access and every streamed
- * population beyond the edge reads the edge cell. */
-typedef enum { VLBM_BC_PERIODIC = 0, VLBM_BC_ZEROGRAD = 1 } vlbm_bc;
+ * population beyond the edge reads the edge cell.  Pinned inflow (x-lo side only, paired with a
+ * zero-gradient x-hi side) is the inflow boundary of Sec. IV H: the ghost cells beyond the side
+ * hold a fixed state W_in (vlbm_set_inflow), whose velocity and flux every stencil reads there and
+ * whose equilibrium populations (Eq. 20, at the link speed of the step) stream into the domain. */
+typedef enum { VLBM_BC_PERIODIC = 0, VLBM_BC_ZEROGRAD = 1, VLBM_BC_INFLOW = 2 } vlbm_bc;
 
 typedef struct {
   int32_t dim;        /* 1 or 2                                                             */
@@ -62,13 +65,20 @@ typedef struct {
 } vlbm_grid;
 
 /* Equations of state of Sec. II C: ideal gas P = (gamma-1) rho e (Eq. 15); polytropic van der
- * Waals P = R rho T / (1 - b rho) - a rho^2, e = cv T - a rho (Eqs. 16-17). */
-typedef enum { VLBM_EOS_IDEAL = 0, VLBM_EOS_VDW = 1 } vlbm_eos_kind;
+ * Waals P = R rho T / (1 - b rho) - a rho^2, e = cv T - a rho (Eqs. 16-17); and, as one of the
+ * generic closures P(rho, e) of Eq. (11), the van der Waals thermal relation with a temperature-
+ * dependent heat capacity c_v(T) = cv + cv1 T + cv2 T^2 (cv > 0, cv1, cv2 >= 0): e = cv T +
+ * cv1 T^2/2 + cv2 T^3/3 - a rho, which satisfies the consistency condition Eq. (12) for any such
+ * c_v.  Its temperature T(rho, e) is found by Newton's method in FP64 on every path (FP32 storage
+ * too), stopping once a step changes T by at most 1e-15 T; a state where 50 steps do not get
+ * there is reported as non-physical. */
+typedef enum { VLBM_EOS_IDEAL = 0, VLBM_EOS_VDW = 1, VLBM_EOS_VDW_CVT = 2 } vlbm_eos_kind;
 
 typedef struct {
-  int32_t kind;                  /* vlbm_eos_kind                 */
-  double gamma;                  /* ideal gas                     */
-  double a, b, R, cv;            /* van der Waals (gamma ignored) */
+  int32_t kind;                  /* vlbm_eos_kind                                  */
+  double gamma;                  /* ideal gas                                      */
+  double a, b, R, cv;            /* van der Waals (gamma ignored)                  */
+  double cv1, cv2;               /* VLBM_EOS_VDW_CVT: c_v(T) = cv + cv1 T + cv2 T^2 */
 } vlbm_eos;
 
 typedef enum { VLBM_FP64 = 0, VLBM_FP32_STORE = 1 } vlbm_precision;
@@ -110,6 +120,13 @@ vlbm_status vlbm_create(const vlbm_grid* grid, const vlbm_eos* eos, const vlbm_p
 
 /* Releases every resource of the handle after its stream has drained.  NULL is accepted. */
 vlbm_status vlbm_destroy(vlbm_t h);
+
+/* State W_in (host array of D+2 conserved values) held by the ghost cells of a pinned-inflow x-lo
+ * side (Sec. IV H: the exact upstream state of the stationary shock).  Required before vlbm_init
+ * on such a grid (else vlbm_init returns VLBM_E_STATE); may be changed between calls.  Returns
+ * VLBM_E_STATE on a grid without a pinned-inflow side and VLBM_E_INVAL for rho <= 0 or a
+ * non-finite or non-physical internal energy.  Synchronises. */
+vlbm_status vlbm_set_inflow(vlbm_t h, const double* W_in);
 
 /* Initial populations f_i = f_i^eq(W0; c0) with c0 = s_max(W0) / CFL (Eqs. 20, 36-37), time 0,
  * step counter 0, history cleared.  W0: (D+2) * ny * nx values.  A replayed schedule (see
@@ -204,6 +221,7 @@ vlbm_status vlbm_get_profile(vlbm_t h, double* ms_total, int64_t* launches);
  *   dJ_dW0:  output, (D+2) ny nx values dJ/dW0 (host or device).
  *   dJ_deos: host[5] output dJ/d(gamma, a, b, R, cv) (the ideal gas uses gamma, van der Waals
  *            a, b, R, cv), or NULL.
+ * Not available on a grid with a pinned-inflow side or with VLBM_EOS_VDW_CVT (VLBM_E_UNSUPPORTED).
  * Afterwards the handle holds the final state of the run (as after vlbm_step).  Device memory:
  * (ceil(n_steps / checkpoint_every) + min(checkpoint_every, n_steps) + 2) population states plus
  * 43 FP64 fields per cell.  Synchronises. */
@@ -237,6 +255,7 @@ vlbm_status vlbm_launches_per_step(vlbm_t h, int32_t* launches);
  *   cuda_stream: stream for the work (NULL: legacy default stream); the call returns without
  *             waiting, beta is valid once the stream reaches this point.
  *
+ * A grid with a pinned-inflow side returns VLBM_E_UNSUPPORTED (there is no handle holding W_in).
  * Limits and behaviour: at most 2,097,152 cells (nx ny, each axis checked first); larger grids
  * return VLBM_E_INVAL.  The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) and sets the kernels' shared-memory attribute, under a lock, so host

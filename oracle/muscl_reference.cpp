@@ -27,12 +27,12 @@ namespace {
 
 // Specific internal energy of (rho, P), the EOS solved for e: ideal gas e = P / ((gamma-1) rho)
 // (Eq. 15); van der Waals T = (P + a rho^2)(1 - b rho) / (R rho) from Eq. (16), then
-// e = cv T - a rho (Eq. 17).
+// e = cv T - a rho (Eq. 17), or e = cv T + cv1 T^2/2 + cv2 T^3/3 - a rho for c_v(T) = cv + cv1 T + cv2 T^2.
 double energy_of(const double* e6, double rho, double P) {
   if (e6[0] == 0.0) return P / ((e6[1] - 1.0) * rho);
-  const double a = e6[2], b = e6[3], R = e6[4], cv = e6[5];
+  const double a = e6[2], b = e6[3], R = e6[4], cv = e6[5], cv1 = e6[6], cv2 = e6[7];
   const double T = (P + a * rho * rho) * (1.0 - b * rho) / (R * rho);
-  return cv * T - a * rho;
+  return cv * T + cv1 * T * T / 2.0 + cv2 * T * T * T / 3.0 - a * rho;
 }
 
 inline double minmod(double l, double r) {
@@ -148,11 +148,21 @@ int orc_muscl_1d(const double* e6, int n, double dx, int bc, double cfl, double 
 // reconstruction and Rusanov flux across every x face (speed |u| + c) and every y face
 // (|v| + c), summed into one update, Heun RK2 in time.  The step is
 // dt = cfl dx / max_cells(|u| + |v| + 2c), the sum form of the unsplit stability limit.
-// W is [rho, rho u, rho v, rho E][y][x].  Returns 0, or 1 if a non-physical state occurred.
-int orc_muscl_2d(const double* e6, int nx, int ny, double dx, double cfl, double t_end, double* W, long* steps) {
+// W is [rho, rho u, rho v, rho E][y][x].  bc4 = (x-lo, x-hi, y-lo, y-hi): 0 periodic, 1 zero-gradient
+// (edge copy), 2 pinned (both ghost cells hold the conserved state win, the inflow boundary of
+// Sec. IV H).  Returns 0, or 1 if a non-physical state occurred.
+int orc_muscl_2d_bc(const double* e6, int nx, int ny, double dx, double cfl, double t_end, const int* bc4,
+                    const double* win, double* W, long* steps) {
   const long N = (long)nx * ny;
   const int PX = nx + 4, PY = ny + 4;
   std::vector<double> V((size_t)4 * PX * PY), U(W, W + 4 * N), U1(4 * N), L(4 * N);
+  double vpin[4] = {0.0, 0.0, 0.0, 0.0};  // primitives (rho, u, v, P) of the pinned state
+  if (win) {
+    const double rho = win[0], u = win[1] / rho, v = win[2] / rho, e = win[3] / rho - 0.5 * (u * u + v * v);
+    double P, c2;
+    orc_eos_eval(e6, rho, e, &P, &c2);
+    vpin[0] = rho, vpin[1] = u, vpin[2] = v, vpin[3] = P;
+  }
   auto vi = [&](int k, int y, int x) -> double& { return V[((size_t)k * PY + y) * PX + x]; };
   // primitives with ghosts; returns max(|u| + |v| + 2c) or -1 if not physical
   auto prim = [&](const std::vector<double>& Uc) -> double {
@@ -171,11 +181,18 @@ int orc_muscl_2d(const double* e6, int nx, int ny, double dx, double cfl, double
         smax = std::max(smax, std::fabs(u) + std::fabs(v) + 2.0 * std::sqrt(std::max(c2, 0.0)));
       }
     if (bad) return -1.0;
+    // ghost cells: periodic images, edge copies, or the pinned state
     for (int k = 0; k < 4; ++k)
       for (int y = 0; y < PY; ++y)
         for (int x = 0; x < PX; ++x) {
-          const int sy = std::min(std::max(y, 2), ny + 1), sx = std::min(std::max(x, 2), nx + 1);
-          if (sy != y || sx != x) vi(k, y, x) = vi(k, sy, sx);
+          int sy = y, sx = x, side = -1;
+          if (x < 2) side = 0;
+          if (x > nx + 1) side = 1;
+          if (side >= 0) sx = bc4[side] == 0 ? (side == 0 ? x + nx : x - nx) : (side == 0 ? 2 : nx + 1);
+          if (y < 2) sy = bc4[2] == 0 ? y + ny : 2;
+          if (y > ny + 1) sy = bc4[3] == 0 ? y - ny : ny + 1;
+          if (sy == y && sx == x) continue;
+          vi(k, y, x) = (side >= 0 && bc4[side] == 2) ? vpin[k] : vi(k, sy, sx);
         }
     return smax;
   };
@@ -254,6 +271,12 @@ int orc_muscl_2d(const double* e6, int nx, int ny, double dx, double cfl, double
   *steps = s;
   std::copy(U.begin(), U.end(), W);
   return t < t_end ? 1 : 0;
+}
+
+// Zero-gradient on every side.
+int orc_muscl_2d(const double* e6, int nx, int ny, double dx, double cfl, double t_end, double* W, long* steps) {
+  const int zg[4] = {1, 1, 1, 1};
+  return orc_muscl_2d_bc(e6, nx, ny, dx, cfl, t_end, zg, nullptr, W, steps);
 }
 
 }  // extern "C"

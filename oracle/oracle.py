@@ -71,6 +71,8 @@ def lib():
                 "orc_dual_get_W": (None, [P, D, D]),
                 "orc_muscl_1d": (I, [D, I, C.c_double, I, C.c_double, C.c_double, D, C.POINTER(C.c_long)]),
                 "orc_muscl_2d": (I, [D, I, I, C.c_double, C.c_double, C.c_double, D, C.POINTER(C.c_long)]),
+                "orc_muscl_2d_bc": (I, [D, I, I, C.c_double, C.c_double, C.c_double, C.POINTER(C.c_int), D, D,
+                                        C.POINTER(C.c_long)]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -86,9 +88,12 @@ def _dp(a: np.ndarray):
 
 
 def eos6(eos: dict) -> np.ndarray:
+    """EOS parameters as the C entry points read them: kind, gamma, a, b, R, cv, cv1, cv2."""
     if eos["kind"] == "ideal":
-        return np.array([0.0, eos["gamma"], 0.0, 0.0, 0.0, 0.0])
-    return np.array([1.0, 1.0 + eos["R"] / eos["cv"], eos["a"], eos["b"], eos["R"], eos["cv"]])
+        return np.array([0.0, eos["gamma"], 0.0, 0.0, 0.0, 0.0, 0.0, 0.0])
+    kind = 2.0 if eos["kind"] == "vdw_cvt" else 1.0
+    return np.array([kind, 1.0 + eos["R"] / eos["cv"], eos["a"], eos["b"], eos["R"], eos["cv"], eos.get("cv1", 0.0),
+                     eos.get("cv2", 0.0)])
 
 
 def prm8(cfl=0.5, beta_mode="sensor", beta_const=1.0, beta_min=0.75, beta_max=1.0, c_sensor=4.0, ducros_eps=1e-6,
@@ -218,8 +223,8 @@ class DualOracleSolver:
         self.nc = dim + 2
         bc4 = (C.c_int * 4)(*[BC_CODE[b] for b in bc])
         self._e6 = eos6(eos)
-        self._de6 = np.zeros(6)
-        for j, key in enumerate(["kind", "gamma", "a", "b", "R", "cv"]):
+        self._de6 = np.zeros(8)
+        for j, key in enumerate(["kind", "gamma", "a", "b", "R", "cv", "cv1", "cv2"]):
             if deos and key in deos:
                 self._de6[j] = deos[key]
         self._p8 = prm8(**params)
@@ -312,14 +317,18 @@ def muscl_1d(eos: dict, W0, dx: float, bc: str, t_end: float, cfl: float = 0.4):
     return W, steps.value
 
 
-def muscl_2d(eos: dict, W0, dx: float, t_end: float, cfl: float = 0.4):
-    """The reference method in 2D (muscl_reference.cpp): unsplit, zero-gradient sides, from W0
-    (4 x ny x nx conserved) at t = 0 to t_end.  Returns (W(t_end), steps)."""
+def muscl_2d(eos: dict, W0, dx: float, t_end: float, cfl: float = 0.4, bc=("zerograd",) * 4, W_in=None):
+    """The reference method in 2D (muscl_reference.cpp): unsplit, from W0 (4 x ny x nx conserved)
+    at t = 0 to t_end, with per-side boundaries (periodic, zero-gradient, or "inflow": ghost cells
+    holding the conserved state W_in).  Returns (W(t_end), steps)."""
     W = np.ascontiguousarray(np.asarray(W0, dtype=np.float64)).copy()
     _, ny, nx = W.shape
     steps = C.c_long(0)
     e6 = eos6(eos)
-    st = lib().orc_muscl_2d(_dp(e6), nx, ny, dx, cfl, t_end, _dp(W), C.byref(steps))
+    bc4 = (C.c_int * 4)(*[BC_CODE[b] for b in bc])
+    win = None if W_in is None else np.ascontiguousarray(np.asarray(W_in, dtype=np.float64).reshape(-1))
+    st = lib().orc_muscl_2d_bc(_dp(e6), nx, ny, dx, cfl, t_end, bc4, None if win is None else _dp(win), _dp(W),
+                               C.byref(steps))
     if st:
         raise ValueError(f"MUSCL reference (2D): non-physical state after {steps.value} steps")
     return W, steps.value

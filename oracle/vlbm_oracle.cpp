@@ -78,13 +78,37 @@ inline T clip01(T x) {  // clip(., 0, 1) of Eqs. (34)-(35)
 // ------------------------------------------------------------------------------------------
 // Equation of state (Sec. II C).
 // ------------------------------------------------------------------------------------------
-enum { EOS_IDEAL = 0, EOS_VDW = 1 };
+enum { EOS_IDEAL = 0, EOS_VDW = 1, EOS_VDW_CVT = 2 };
 
 template <class T>
 struct Eos {
   int kind;
   T gamma, a, b, R, cv;
+  T cv1, cv2;  // EOS_VDW_CVT: c_v(T) = cv + cv1 T + cv2 T^2
 };
+
+// Caloric part of the non-polytropic van der Waals gas (EOS_VDW_CVT): the heat capacity
+// c_v(T) = cv + cv1 T + cv2 T^2 integrates to E(T) = cv T + cv1 T^2/2 + cv2 T^3/3, and
+// e = E(T) - a rho.  For the thermal relation of Eq. (16), (dP/dT)_rho = R rho / (1 - b rho), so
+// the consistency condition Eq. (12) gives (de/drho)_T = [P - T (dP/dT)_rho] / rho^2 = -a whatever
+// c_v(T) is: any positive c_v(T) is admissible.  The paper's Eq. (11) is this P(rho, e) with T(rho, e)
+// from inverting E(T) = e + a rho, done here by Newton's method from T0 = (e + a rho)/cv; E is
+// increasing and convex for cv > 0, cv1, cv2 >= 0, so E(T0) >= e + a rho and the iterates fall
+// monotonically onto the root.  The iteration stops when a step changes T by at most 1e-15 T;
+// after 50 steps without that, T is returned as NaN (a non-physical state).
+template <class T>
+T vdw_cvt_temperature(const Eos<T>& q, T rho, T e) {
+  T target = e + q.a * rho;
+  T temp = target / q.cv;
+  for (int it = 0; it < 50; ++it) {
+    T E = q.cv * temp + q.cv1 * temp * temp / 2.0 + q.cv2 * temp * temp * temp / 3.0;
+    T cvT = q.cv + q.cv1 * temp + q.cv2 * temp * temp;
+    T step = (E - target) / cvT;
+    temp = temp - step;
+    if (std::fabs(val(step)) <= 1e-15 * std::fabs(val(temp))) return temp;
+  }
+  return T(std::nan(""));
+}
 
 // Pressure P(rho, e) (Eq. 11) and frozen sound speed c_s^2 = P_rho + P P_e / rho^2 (Eq. 13).
 // Ideal gas: Eq. (15).  Polytropic van der Waals: Eqs. (16)-(17), with the caloric relation
@@ -97,13 +121,15 @@ void eos_eval(const Eos<T>& q, T rho, T e, T* P, T* cs2) {
     *cs2 = q.gamma * (q.gamma - 1.0) * e;
     return;
   }
-  T temp = (e + q.a * rho) / q.cv;  // Eq. (17) solved for T
+  // T from the caloric relation: Eq. (17) solved for T, or the Newton inversion of E(T)
+  T temp = q.kind == EOS_VDW_CVT ? vdw_cvt_temperature(q, rho, e) : (e + q.a * rho) / q.cv;
+  T cvT = q.kind == EOS_VDW_CVT ? q.cv + q.cv1 * temp + q.cv2 * temp * temp : q.cv;  // c_v at T
   T omb = 1.0 - q.b * rho;
   T p = q.R * rho * temp / omb - q.a * rho * rho;                        // Eq. (16)
   T dP_dT_rho = q.R * rho / omb;                                         // (dP/dT)_rho
   T dP_drho_T = q.R * temp / (omb * omb) - 2.0 * q.a * rho;              // (dP/drho)_T
-  T dT_drho_e = q.a / q.cv;                                              // from Eq. (17)
-  T dT_de_rho = 1.0 / q.cv;
+  T dT_drho_e = q.a / cvT;                                               // from e = E(T) - a rho
+  T dT_de_rho = 1.0 / cvT;
   T P_rho = dP_drho_T + dP_dT_rho * dT_drho_e;  // (dP/drho)_e
   T P_e = dP_dT_rho * dT_de_rho;                // (dP/de)_rho
   *P = p;
@@ -117,7 +143,7 @@ void eos_eval(const Eos<T>& q, T rho, T e, T* P, T* cs2) {
 inline double fundamental_derivative(const Eos<double>& q, double rho, double e) {
   double P, cs2;
   eos_eval(q, rho, e, &P, &cs2);
-  Eos<Dual> qd{q.kind, Dual(q.gamma), Dual(q.a), Dual(q.b), Dual(q.R), Dual(q.cv)};
+  Eos<Dual> qd{q.kind, Dual(q.gamma), Dual(q.a), Dual(q.b), Dual(q.R), Dual(q.cv), Dual(q.cv1), Dual(q.cv2)};
   Dual Pd, cs2d;
   eos_eval(qd, Dual(rho, 1.0), Dual(e, P / (rho * rho)), &Pd, &cs2d);
   return 1.0 + rho / (2.0 * cs2) * cs2d.d;
@@ -550,7 +576,7 @@ struct Solver {
 using namespace orc;
 
 // ------------------------------------------------------------------------------------------
-// C entry points for the Python test harness (ctypes).  eos6 = {kind, gamma, a, b, R, cv};
+// C entry points for the Python test harness (ctypes).  eos6 = {kind, gamma, a, b, R, cv, cv1, cv2};
 // prm8 = {cfl, beta_mode, beta_const, beta_min, beta_max, c_sensor, ducros_eps, retarget_every};
 // field arrays are [component][y][x]; populations [i][k][y][x].
 // ------------------------------------------------------------------------------------------
@@ -563,6 +589,8 @@ static Eos<T> make_eos(const double* e6, const double* de6) {
   q.b = T(e6[3]);
   q.R = T(e6[4]);
   q.cv = T(e6[5]);
+  q.cv1 = T(e6[6]);
+  q.cv2 = T(e6[7]);
   if (de6) {
     if constexpr (std::is_same<T, Dual>::value) {
       q.gamma.d = de6[1];
@@ -570,6 +598,8 @@ static Eos<T> make_eos(const double* e6, const double* de6) {
       q.b.d = de6[3];
       q.R.d = de6[4];
       q.cv.d = de6[5];
+      q.cv1.d = de6[6];
+      q.cv2.d = de6[7];
     }
   }
   return q;

@@ -44,6 +44,7 @@ struct vlbm_s {
   double* fscratch = nullptr;  // populations readback (lazily allocated)
   double* fields = nullptr;    // FP64 strips: W, u, Q kept from the maxima pass (14 planes)
   bool initialised = false;
+  bool inflow_set = false;     // pinned-inflow grids: vlbm_set_inflow has supplied W_in
   bool unpulled = true;        // the current buffer holds equilibrium populations in place
   bool last_step_pulled = true;
   long long n_host = 0;        // steps completed, as of the last synchronisation
@@ -312,13 +313,17 @@ bool valid_problem(const vlbm_grid* grid, const vlbm_eos* eos, const vlbm_params
   if (nx < 1 || ny < 1) return false;
   if (!(grid->x1 > grid->x0)) return false;
   for (int j = 0; j < 4; ++j)
-    if (grid->bc[j] != VLBM_BC_PERIODIC && grid->bc[j] != VLBM_BC_ZEROGRAD) return false;
+    if (grid->bc[j] != VLBM_BC_PERIODIC && grid->bc[j] != VLBM_BC_ZEROGRAD && !(j == 0 && grid->bc[j] == VLBM_BC_INFLOW))
+      return false;
+  // a pinned-inflow x-lo side pairs with a zero-gradient (outflow) x-hi side
+  if (grid->bc[0] == VLBM_BC_INFLOW && grid->bc[1] != VLBM_BC_ZEROGRAD) return false;
   if ((grid->bc[0] == VLBM_BC_PERIODIC) != (grid->bc[1] == VLBM_BC_PERIODIC)) return false;
   if (grid->dim == 2 && (grid->bc[2] == VLBM_BC_PERIODIC) != (grid->bc[3] == VLBM_BC_PERIODIC)) return false;
   if (eos->kind == VLBM_EOS_IDEAL) {
     if (!(eos->gamma > 1.0)) return false;
-  } else if (eos->kind == VLBM_EOS_VDW) {
+  } else if (eos->kind == VLBM_EOS_VDW || eos->kind == VLBM_EOS_VDW_CVT) {
     if (!(eos->a >= 0.0 && eos->b >= 0.0 && eos->R > 0.0 && eos->cv > 0.0)) return false;
+    if (eos->kind == VLBM_EOS_VDW_CVT && !(eos->cv1 >= 0.0 && eos->cv2 >= 0.0)) return false;
   } else {
     return false;
   }
@@ -349,7 +354,7 @@ void make_kparams(const vlbm_grid* grid, const vlbm_eos* eos, const vlbm_params*
   p.b = eos->b;
   p.R = eos->R;
   p.cv = eos->cv;
-  p.inv_cv = eos->kind == VLBM_EOS_VDW ? 1.0 / eos->cv : 0.0;
+  p.inv_cv = eos->kind != VLBM_EOS_IDEAL ? 1.0 / eos->cv : 0.0;
   p.cfl = params->cfl;
   p.beta_mode = params->beta_mode;
   p.beta_const = params->beta_const;
@@ -378,6 +383,12 @@ void make_kparams(const vlbm_grid* grid, const vlbm_eos* eos, const vlbm_params*
   c.eps_lat = p.ducros_eps * (2.0 * p.dx) * (2.0 * p.dx);
   c.c_chi2 = p.c_sensor / 512.0;
   c.c_chi1 = p.c_sensor / (4.0 * std::sqrt(3.0));
+  const bool cvt = eos->kind == VLBM_EOS_VDW_CVT;
+  c.cv0 = eos->kind != VLBM_EOS_IDEAL ? eos->cv : 0.0;
+  c.cv1 = cvt ? eos->cv1 : 0.0;
+  c.cv2 = cvt ? eos->cv2 : 0.0;
+  c.cv1h = c.cv1 / 2.0;
+  c.cv2t = c.cv2 / 3.0;
   Coef<float>& f = p.cf;
   f.gamma = (float)c.gamma;
   f.gm1 = (float)c.gm1;
@@ -394,6 +405,11 @@ void make_kparams(const vlbm_grid* grid, const vlbm_eos* eos, const vlbm_params*
   f.eps_lat = (float)c.eps_lat;
   f.c_chi2 = (float)c.c_chi2;
   f.c_chi1 = (float)c.c_chi1;
+  f.cv0 = (float)c.cv0;
+  f.cv1 = (float)c.cv1;
+  f.cv2 = (float)c.cv2;
+  f.cv1h = (float)c.cv1h;
+  f.cv2t = (float)c.cv2t;
 }
 
 }  // namespace vlbm
@@ -540,8 +556,32 @@ vlbm_status vlbm_set_dt_schedule(vlbm_t h, const double* c_host, int64_t n) {
   return VLBM_OK;
 }
 
+vlbm_status vlbm_set_inflow(vlbm_t h, const double* W_in) {
+  if (!h || !W_in) return VLBM_E_INVAL;
+  if (h->p.bc[0] != VLBM_BC_INFLOW) return VLBM_E_STATE;
+  const KParams& p = h->p;
+  for (int k = 0; k < p.nc; ++k)
+    if (!std::isfinite(W_in[k])) return VLBM_E_INVAL;
+  const double rho = W_in[0];
+  double usq = 0.0;
+  for (int a = 0; a < p.dim; ++a) usq += (W_in[1 + a] / rho) * (W_in[1 + a] / rho);
+  const double e = W_in[p.nc - 1] / rho - 0.5 * usq;
+  if (!(rho > 0.0) || !std::isfinite(e)) return VLBM_E_INVAL;
+  if (p.eos_kind == VLBM_EOS_IDEAL && !(e > 0.0)) return VLBM_E_INVAL;
+  if (p.eos_kind != VLBM_EOS_IDEAL && !(1.0 - p.b * rho > 0.0)) return VLBM_E_INVAL;
+  VLBM_TRY(cudaStreamSynchronize(h->stream));
+  for (int k = 0; k < 4; ++k) {
+    h->p.cd.win[k] = k < p.nc ? W_in[k] : 0.0;
+    h->p.cf.win[k] = (float)h->p.cd.win[k];
+  }
+  h->inflow_set = true;
+  destroy_graphs(h);  // the graphs captured the kernel parameters
+  return VLBM_OK;
+}
+
 vlbm_status vlbm_init(vlbm_t h, const double* W0) {
   if (!h || !W0) return VLBM_E_INVAL;
+  if (h->p.bc[0] == VLBM_BC_INFLOW && !h->inflow_set) return VLBM_E_STATE;
   const size_t wbytes = (size_t)h->p.nc * h->p.plane * sizeof(double);
   const double* src = W0;
   if (!is_device_ptr(W0)) {
@@ -864,6 +904,8 @@ vlbm_status vlbm_get_profile(vlbm_t h, double* ms_total, int64_t* launches) {
 vlbm_status vlbm_adjoint(vlbm_t h, const double* W0, int64_t n_steps, int32_t checkpoint_every, const double* dJ_dWT,
                          double* dJ_dW0, double* dJ_deos) {
   if (!h || !W0 || !dJ_dWT || !dJ_dW0 || n_steps < 1 || checkpoint_every < 1) return VLBM_E_INVAL;
+  if (h->p.bc[0] == VLBM_BC_INFLOW) return VLBM_E_UNSUPPORTED;  // the adjoint has no ghost cells
+  if (h->p.eos_kind == VLBM_EOS_VDW_CVT) return VLBM_E_UNSUPPORTED;  // nor a Newton-inversion Jacobian
   auto& A = h->adj;
   const KParams& p = h->p;
   // population states are kept in the handle's storage precision (FP64, or FP32 deviations);

@@ -15,7 +15,8 @@ namespace vlbm {
 // index rules
 // ------------------------------------------------------------------------------------------
 // Cell index read at position j along an axis of n cells: wrap (periodic) or clamp to the edge
-// (zero-gradient).
+// (zero-gradient).  Positions beyond a pinned-inflow side (lo == 2) hold the ghost state, which
+// the callers supply themselves; the clamp only keeps any index inside the buffer.
 __device__ __forceinline__ int nb_index(int j, int n, int lo, int hi) {
   if (j < 0) {
     if (lo == 0) {
@@ -36,7 +37,8 @@ __device__ __forceinline__ int nb_index(int j, int n, int lo, int hi) {
 
 // Position at which a stencil quantity "at" position j is evaluated: the edge cell beyond a
 // zero-gradient side (the ghost replicates the edge cell), j itself otherwise (periodic sides are
-// unwrapped; the region holds the wrapped values there).
+// unwrapped, the region holds the wrapped values there; beyond a pinned-inflow side the region
+// holds the ghost cells' own values).
 __device__ __forceinline__ int centre_pos(int j, int n, int lo, int hi) {
   if (j < 0 && lo == 1) return 0;
   if (j >= n && hi == 1) return n - 1;
@@ -130,14 +132,39 @@ __device__ __forceinline__ void eos_eval(const KParams& p, const Coef<E>& c, E r
   if (p.eos_kind == 0) {  // ideal gas, Eq. (15)
     P = c.gm1 * rho * e;
     cs2 = c.ggm1 * e;
-  } else {  // polytropic van der Waals, Eqs. (16)-(17); c_s^2 by Eq. (13)
-    const E T = (e + c.a * rho) * c.inv_cv;
+  } else {  // van der Waals, Eqs. (16)-(17); c_s^2 by Eq. (13)
+    E T, a_inv_cv = c.a_inv_cv, inv_cv = c.inv_cv;
+    if (p.eos_kind == 2) {
+      // c_v(T) = cv + cv1 T + cv2 T^2, e = E(T) - a rho with E(T) = cv T + cv1 T^2/2 + cv2 T^3/3:
+      // Newton's method on E(T) = e + a rho from T0 = (e + a rho)/cv (E is increasing and convex, so
+      // the iterates fall monotonically onto the root); stops when a step changes T by at most
+      // 1e-15 T, else after 50 steps T is NaN and the state is reported non-physical
+      const E target = e + c.a * rho;
+      T = target * c.inv_cv;
+      bool conv = false;
+#pragma unroll 1
+      for (int it = 0; it < 50; ++it) {
+        const E ET = T * fma(T, fma(T, c.cv2t, c.cv1h), c.cv0);
+        const E cvT = fma(T, fma(T, c.cv2, c.cv1), c.cv0);
+        const E step = div_(ET - target, cvT);
+        T -= step;
+        if (fabs(step) <= (E)1e-15 * fabs(T)) {
+          conv = true;
+          break;
+        }
+      }
+      if (!conv) T = (E)NAN;
+      inv_cv = rcp_(fma(T, fma(T, c.cv2, c.cv1), c.cv0));  // 1 / c_v(T)
+      a_inv_cv = c.a * inv_cv;
+    } else {
+      T = (e + c.a * rho) * c.inv_cv;
+    }
     const E inv_omb = rcp_((E)1 - c.b * rho);
     const E RT_omb = c.R * T * inv_omb;
     P = rho * RT_omb - c.a * rho * rho;
-    const E dPdT = c.R * rho * inv_omb;                                       // (dP/dT)_rho
-    const E P_rho = RT_omb * inv_omb - (E)2 * c.a * rho + dPdT * c.a_inv_cv;  // (dP/drho)_e
-    const E P_e = dPdT * c.inv_cv;                                            // (dP/de)_rho
+    const E dPdT = c.R * rho * inv_omb;                                     // (dP/dT)_rho
+    const E P_rho = RT_omb * inv_omb - (E)2 * c.a * rho + dPdT * a_inv_cv;  // (dP/drho)_e
+    const E P_e = dPdT * inv_cv;                                            // (dP/de)_rho
     cs2 = P_rho + P * inv_rho * inv_rho * P_e;
   }
 }
@@ -206,13 +233,60 @@ struct Store<float> {
   static constexpr bool kOffset = true;
 };
 
+// ------------------------------------------------------------------------------------------
+// pinned inflow (x-lo side, VLBM_BC_INFLOW; Sec. IV H): every ghost cell x < 0 holds the state
+// W_in; its populations are the equilibrium of W_in (Eq. 20) at the link speed of the stored
+// populations, 1/c = ginv (a relaxed ghost stays that equilibrium, reprojected to the new speed).
+// ------------------------------------------------------------------------------------------
+template <int D, class M>
+__device__ __forceinline__ void ghost_state(const KParams& p, M (&W)[D + 2], M (&u)[D], M (&Qf)[D][D + 2]) {
+  const Coef<M>& co = coef<M>(p);
+#pragma unroll
+  for (int k = 0; k < D + 2; ++k) W[k] = co.win[k];
+  M cs;
+  prim_flux<D, M, false>(p, W, u, Qf, cs);
+}
+
+// Population i of a ghost cell, in the storage representation (FP32 storage: minus W_ref/Q; wq
+// holds Q W_ref/Q per component).
+template <int D, class M, bool OFFSET>
+__device__ __forceinline__ void ghost_population(const KParams& p, const M* wq, M ginv, int i, M (&v)[D + 2]) {
+  M W[D + 2], u[D], Qf[D][D + 2];
+  ghost_state<D, M>(p, W, u, Qf);
+  constexpr M inv_q = (M)1 / (M)(2 * D);
+#pragma unroll
+  for (int k = 0; k < D + 2; ++k) {
+    M ciQ = (M)sig_x(i) * Qf[0][k];
+    if constexpr (D == 2) ciQ += (M)sig_y(i) * Qf[1][k];
+    v[k] = (OFFSET ? W[k] - wq[k] : W[k]) * inv_q + (M)0.5 * ginv * ciQ;
+  }
+}
+
+// The values of a pinned-inflow ghost cell, the same for every ghost and every thread of a launch:
+// populations (storage representation), W, u, Q.  Filled once per CTA (fill_ghost_tab, one thread,
+// then a barrier) into shared memory, so that the ghost paths of the kernels are plain loads.
+template <int D, class M>
+struct GhostTab {
+  M f[2 * D][D + 2];
+  M W[D + 2], u[D], Q[D][D + 2];
+};
+
+template <int D, class M, bool OFFSET>
+__device__ __noinline__ void fill_ghost_tab(const KParams& p, const M* wq, M ginv, GhostTab<D, M>& g) {
+#pragma unroll 1
+  for (int i = 0; i < 2 * D; ++i) ghost_population<D, M, OFFSET>(p, wq, ginv, i, g.f[i]);
+  ghost_state<D, M>(p, g.W, g.u, g.Q);
+}
+
 // Loads the populations of cell (cx, cy), pulled across the links (or in place), into fr[i][k].
 // Layout [i][y][x][4]: one vector access per direction.  `interior`: the caller guarantees that
-// (cx, cy) and its four neighbours lie inside the domain (no boundary rule needed).  Offsets are
-// 32-bit (vlbm_create bounds 2D * 4 * nx * ny below 2^31).
+// (cx, cy) and its four neighbours lie inside the domain (no boundary rule needed).  gpop: the
+// ghost populations [i][k] of a pinned-inflow side (GhostTab::f), nullptr without one; a pull from
+// beyond that side takes them.  Offsets are 32-bit (vlbm_create bounds 2D * 4 * nx * ny below 2^31).
 template <int D, class S>
 __device__ __forceinline__ void load_cell(const S* __restrict__ fin, const KParams& p, int cx, int cy, int pulled,
-                                          bool interior, typename Store<S>::M (&fr)[2 * D][D + 2]) {
+                                          bool interior, typename Store<S>::M (&fr)[2 * D][D + 2],
+                                          const typename Store<S>::M* gpop = nullptr) {
   using M = typename Store<S>::M;
   constexpr int NC = D + 2, Q = 2 * D;
   const int plane = (int)p.plane;
@@ -224,6 +298,11 @@ __device__ __forceinline__ void load_cell(const S* __restrict__ fin, const KPara
         sx = cx - sig_x(i);
         sy = cy - sig_y(i);
       } else {
+        if (gpop && cx - sig_x(i) < 0) {
+#pragma unroll
+          for (int k = 0; k < NC; ++k) fr[i][k] = gpop[i * NC + k];
+          continue;
+        }
         sx = nb_index(cx - sig_x(i), p.nx, p.bc[0], p.bc[1]);
         if (D == 2) sy = nb_index(cy - sig_y(i), p.ny, p.bc[2], p.bc[3]);
       }

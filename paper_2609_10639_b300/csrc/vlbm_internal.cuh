@@ -54,6 +54,9 @@ struct Coef {
   M eps_lat;                    // Ducros regulariser (Eqs. 32-33) in units of unscaled central
                                 // differences, eps (2 dx)^2: theta = D^2 / (D^2 + V^2 + eps_lat)
                                 // with D, V the dilatation and vorticity times 2 dx
+  M win[4];                     // state W_in of the pinned-inflow ghost cells (x-lo side)
+  M cv0, cv1, cv2, cv1h, cv2t;  // non-polytropic van der Waals: c_v(T) = cv0 + cv1 T + cv2 T^2,
+                                // cv1 / 2 and cv2 / 3 (the integral E(T))
 };
 
 // Constant per-solver parameters, passed to kernels by value.
@@ -61,10 +64,10 @@ struct KParams {
   int dim, nc, q;
   int nx, ny;
   long long plane;  // nx * ny
-  int bc[4];        // x-lo, x-hi, y-lo, y-hi: 0 periodic, 1 zero-gradient
+  int bc[4];        // x-lo, x-hi, y-lo, y-hi: 0 periodic, 1 zero-gradient, 2 pinned inflow (x-lo only)
   double dx, inv2dx;
   int eos_kind;
-  double gamma, a, b, R, cv, inv_cv;
+  double gamma, a, b, R, cv, inv_cv;  // eos_kind: 0 ideal, 1 van der Waals, 2 van der Waals with c_v(T)
   double cfl;
   int beta_mode;
   double beta_const, beta_min, beta_max, c_sensor, ducros_eps;

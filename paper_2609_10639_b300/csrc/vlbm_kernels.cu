@@ -57,6 +57,13 @@ __global__ void __launch_bounds__(NT) k_reduce(const S* __restrict__ fin, Scalar
   M wq[NC];
 #pragma unroll
   for (int k = 0; k < NC; ++k) wq[k] = StepScalars<M>::wq(sc, k);
+  // pinned inflow: the ghost values, with the stored populations' link speed c_prev
+  __shared__ GhostTab<D, M> gtab;
+  const bool inflow = p.bc[0] == 2;
+  if (inflow) {
+    if (threadIdx.x == 0) fill_ghost_tab<D, M, Store<S>::kOffset>(p, wq, (M)(1.0 / sc->c_prev), gtab);
+    __syncthreads();
+  }
   typename R::T v[kNV];
 #pragma unroll
   for (int j = 0; j < kNV; ++j) v[j] = typename R::T(0);
@@ -64,7 +71,7 @@ __global__ void __launch_bounds__(NT) k_reduce(const S* __restrict__ fin, Scalar
   for (long long cell = (long long)blockIdx.x * NT + threadIdx.x; cell < p.plane; cell += (long long)gridDim.x * NT) {
     const int cx = (int)(cell % p.nx), cy = (int)(cell / p.nx);
     M fr[2 * D][NC], W[NC], u[D], Qf[D][NC], cs;
-    load_cell<D, S>(fin, p, cx, cy, pulled, false, fr);
+    load_cell<D, S>(fin, p, cx, cy, pulled, false, fr, inflow ? &gtab.f[0][0] : nullptr);
     moments<D, M, Store<S>::kOffset>(fr, wq, W);
     bad |= !prim_flux<D, M, true>(p, W, u, Qf, cs);
     cell_maxima<D, M>(u, cs, Qf, v);
@@ -231,6 +238,16 @@ __global__ void __launch_bounds__(TX * TY, 2) k_tile(const S* __restrict__ fin, 
   // boundary rule is evaluated (uniform per CTA).
   const bool interior = x0 - H - 1 >= 0 && x0 + TX + H + 1 <= p.nx &&
                         (D == 1 || (y0 - HY - 1 >= 0 && y0 + TY + HY + 1 <= p.ny));
+  // pinned inflow: the ghost values, at the link speed of the stored populations (readback:
+  // c_prev; in a step, after the link-speed kernel: c_new r)
+  __shared__ GhostTab<D, M> gtab;
+  const bool inflow = p.bc[0] == 2;
+  if (inflow) {
+    if (threadIdx.x == 0)
+      fill_ghost_tab<D, M, OFF>(p, wq, BETA_OUT ? (M)(1.0 / sc->c_prev) : StepScalars<M>::inv_c(sc) / StepScalars<M>::r(sc),
+                                gtab);
+    __syncthreads();
+  }
 
   // ---- phase A: populations, primitives and flux over the region (row-major, coalesced) ----
   for (int idx = threadIdx.x; idx < RX * RY; idx += NT) {
@@ -239,9 +256,22 @@ __global__ void __launch_bounds__(TX * TY, 2) k_tile(const S* __restrict__ fin, 
     const int cx = interior ? px : nb_index(px, p.nx, p.bc[0], p.bc[1]);
     const int cy = (D == 2) ? (interior ? py : nb_index(py, p.ny, p.bc[2], p.bc[3])) : 0;
     M fr[Q][NC], W[NC], u[D], Qf[D][NC], cs;
-    load_cell<D, S>(fin, p, cx, cy, pulled, interior, fr);
-    moments<D, M, OFF>(fr, wq, W);
-    prim_flux<D, M, false>(p, W, u, Qf, cs);
+    if (!interior && inflow && px < 0) {  // ghost cell of the pinned-inflow side
+#pragma unroll
+      for (int k = 0; k < NC; ++k) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) fr[i][k] = gtab.f[i][k];
+        W[k] = gtab.W[k];
+#pragma unroll
+        for (int a = 0; a < D; ++a) Qf[a][k] = gtab.Q[a][k];
+      }
+#pragma unroll
+      for (int a = 0; a < D; ++a) u[a] = gtab.u[a];
+    } else {
+      load_cell<D, S>(fin, p, cx, cy, pulled, interior, fr, inflow ? &gtab.f[0][0] : nullptr);
+      moments<D, M, OFF>(fr, wq, W);
+      prim_flux<D, M, false>(p, W, u, Qf, cs);
+    }
 #pragma unroll
     for (int a = 0; a < D; ++a) {
       s_u[a * RY * RX + idx] = u[a];
@@ -551,6 +581,13 @@ __global__ void __launch_bounds__(NT) k_get_W(const S* __restrict__ fin, const S
   for (int i = 0; i < Q; ++i) {
     int sx = cx, sy = cy;
     if (pulled) {
+      if (p.bc[0] == 2 && cx - sig_x(i) < 0) {  // from a pinned-inflow ghost cell, at c_prev
+        double g[NC];
+        ghost_population<D, double, false>(p, nullptr, 1.0 / sc->c_prev, i, g);
+#pragma unroll
+        for (int k = 0; k < NC; ++k) acc[k] += g[k];
+        continue;
+      }
       sx = nb_index(cx - sig_x(i), p.nx, p.bc[0], p.bc[1]);
       if (D == 2) sy = nb_index(cy - sig_y(i), p.ny, p.bc[2], p.bc[3]);
     }
@@ -575,6 +612,13 @@ __global__ void __launch_bounds__(NT) k_get_f(const S* __restrict__ fin, const S
   for (int i = 0; i < Q; ++i) {
     int sx = cx, sy = cy;
     if (pulled) {
+      if (p.bc[0] == 2 && cx - sig_x(i) < 0) {  // from a pinned-inflow ghost cell, at c_prev
+        double g[NC];
+        ghost_population<D, double, false>(p, nullptr, 1.0 / sc->c_prev, i, g);
+#pragma unroll
+        for (int k = 0; k < NC; ++k) f[(long long)(i * NC + k) * p.plane + cell] = g[k];
+        continue;
+      }
       sx = nb_index(cx - sig_x(i), p.nx, p.bc[0], p.bc[1]);
       if (D == 2) sy = nb_index(cy - sig_y(i), p.ny, p.bc[2], p.bc[3]);
     }
@@ -833,6 +877,7 @@ extern "C" vlbm_status vlbm_beta_noalloc(const vlbm_grid* grid, const vlbm_eos* 
   using namespace vlbm;
   if (!grid || !eos || !params || !f || !beta) return VLBM_E_INVAL;
   if (!valid_problem(grid, eos, params)) return VLBM_E_INVAL;
+  if (grid->bc[0] == VLBM_BC_INFLOW) return VLBM_E_UNSUPPORTED;  // no pinned state to read from
   // beyond the fixed scratch: rejected (each axis first, so that nx * ny cannot overflow)
   const long long nx = grid->nx, ny = grid->dim == 1 ? 1 : grid->ny;
   if (nx > kNoallocMaxCells || ny > kNoallocMaxCells || nx * ny > kNoallocMaxCells) return VLBM_E_INVAL;

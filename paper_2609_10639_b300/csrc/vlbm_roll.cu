@@ -71,8 +71,10 @@ __device__ __forceinline__ int ring(int r, int base) {
 // FP32 storage: 1024 resident threads per SM (64 registers) to hide memory latency (0.46 vs
 // 0.73 ms per two-pass step kernel at 4096^2 with half of them); FP64 is bound by its FP64 pipe
 // and runs two CTAs of up to 128 registers per SM, so that one CTA's stage S1 (loads only, with
-// W, u, Q kept by the maxima pass) overlaps the other's arithmetic.
-template <class S, bool LOOK, int XW, int RR>
+// W, u, Q kept by the maxima pass) overlaps the other's arithmetic.  INFLOW: the grid has a
+// pinned-inflow x-lo side (a separate instantiation: the ghost paths cost the FP32 kernel register
+// spills, 76 bytes, which the other grids need not pay).
+template <class S, bool LOOK, int XW, int RR, bool INFLOW>
 __global__ void __launch_bounds__(XW * RR, sizeof(S) == 4 ? 1024 / (XW * RR) : 512 / (XW * RR)) k_roll(const S* __restrict__ fin, S* __restrict__ fout,
                                                   Scalars* __restrict__ sc, const KParams p, const int pulled,
                                                   const typename Store<S>::M* __restrict__ invM_src,
@@ -92,11 +94,14 @@ __global__ void __launch_bounds__(XW * RR, sizeof(S) == 4 ? 1024 / (XW * RR) : 5
 
   const Coef<M>& co = coef<M>(p);
   const int tx = threadIdx.x % XW, ty = threadIdx.x / XW;
-  const bool zx = p.bc[0] == 1, zy = p.bc[2] == 1;  // zero-gradient in x / y (both sides alike)
-  // centre_pos of a row.  Both sides of an axis share their rule (checked at vlbm_create), so a
-  // zero-gradient axis clamps and a periodic one keeps the unwrapped index; the FP32 kernel takes
-  // that branch-free form (0.495 against 0.527 ms per look-ahead step kernel at 4096^2), the FP64
-  // kernel the general one (4.90 against 4.95 ms).
+  // zero-gradient sides in x (each side alone: a pinned-inflow x-lo side pairs with a
+  // zero-gradient x-hi side) and in y (both sides alike, checked at vlbm_create)
+  const bool zxl = p.bc[0] == 1, zxh = p.bc[1] == 1, zy = p.bc[2] == 1;
+  constexpr bool gx = INFLOW;  // pinned-inflow x-lo side: ghost cells x < 0 hold W_in
+  // centre_pos of a row.  Both sides of the y axis share their rule, so a zero-gradient axis
+  // clamps and a periodic one keeps the unwrapped index; the FP32 kernel takes that branch-free
+  // form (0.495 against 0.527 ms per look-ahead step kernel at 4096^2), the FP64 kernel the
+  // general one (4.90 against 4.95 ms).
   auto yc = [&](int r) -> int {
     if constexpr (sizeof(S) == 4) return zy ? min(max(r, 0), p.ny - 1) : r;
     else return centre_pos(r, p.ny, p.bc[2], p.bc[3]);
@@ -110,6 +115,12 @@ __global__ void __launch_bounds__(XW * RR, sizeof(S) == 4 ? 1024 / (XW * RR) : 5
   }
   const M r_c = StepScalars<M>::r(sc), inv_c = StepScalars<M>::inv_c(sc);
   const int slot_n = (int)(sc->n & 1);
+  // pinned inflow: the ghost values at the link speed of the stored populations, c_new r (read
+  // after the barrier at the start of the first segment)
+  __shared__ GhostTab<2, M> gtab;
+  if constexpr (INFLOW) {
+    if (threadIdx.x == 0) fill_ghost_tab<2, M, OFF>(p, wq, inv_c / r_c, gtab);
+  }
 
   using R = Red<M>;
   typename R::T vmax[kNV];
@@ -140,12 +151,20 @@ __global__ void __launch_bounds__(XW * RR, sizeof(S) == 4 ? 1024 / (XW * RR) : 5
   const int base = y0 - H;
   // strip positions or their pull sources outside [0, nx): boundary rules needed in x
   const bool xedge = xs - 1 < 0 || xs + XW + 1 > p.nx;
-  const bool x_in = px >= 0 && px < p.nx;
   // strip index of the value read at column px + d (the edge cell beyond a zero-gradient side)
   auto xi = [&](int d) -> int {
-    if constexpr (sizeof(S) == 4) return (xedge && zx) ? min(max(px + d, 0), p.nx - 1) - xs : tx + d;
-    else return xedge ? centre_pos(px + d, p.nx, p.bc[0], p.bc[1]) - xs : tx + d;
+    if constexpr (sizeof(S) == 4) {
+      if (!xedge) return tx + d;
+      int j = px + d;
+      if (zxl) j = max(j, 0);
+      if (zxh) j = min(j, p.nx - 1);
+      return j - xs;
+    } else {
+      return xedge ? centre_pos(px + d, p.nx, p.bc[0], p.bc[1]) - xs : tx + d;
+    }
   };
+  // positions beyond a zero-gradient x side hold no values of their own (reads land on the edge)
+  const bool x_void = (zxl && px < 0) || (zxh && px >= p.nx);
   __syncthreads();  // the rings of a previous segment are no longer read
 
   for (int F = base; F - RR - (LOOK ? 1 : 0) < yend; F += RR) {
@@ -175,11 +194,30 @@ __global__ void __launch_bounds__(XW * RR, sizeof(S) == 4 ? 1024 / (XW * RR) : 5
         const int cy = nb_index(r, p.ny, p.bc[2], p.bc[3]);
         const int cx = xedge ? nb_index(px, p.nx, p.bc[0], p.bc[1]) : px;
         const bool inner = !xedge && cy >= 1 && cy < p.ny - 1;
-        load_cell<2, S>(fin, p, cx, cy, pulled, inner, fnew);
+        const bool ghost = gx && px < 0;  // a ghost cell of the pinned-inflow side
         M W[4], u[2], Qf[2][4], cs;
         bool have = false;
+        if constexpr (INFLOW) {
+          if (ghost) {
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) fnew[i][k] = gtab.f[i][k];
+            W[k] = gtab.W[k];
+            Qf[0][k] = gtab.Q[0][k];
+            Qf[1][k] = gtab.Q[1][k];
+          }
+          u[0] = gtab.u[0];
+          u[1] = gtab.u[1];
+          have = true;
+          } else {
+            load_cell<2, S>(fin, p, cx, cy, pulled, inner, fnew, &gtab.f[0][0]);
+          }
+        } else {
+          load_cell<2, S>(fin, p, cx, cy, pulled, inner, fnew);
+        }
         if constexpr (!LOOK && std::is_same<M, double>::value) {
-          if (fields) {  // W, u, Q of this state, stored by the maxima pass
+          if (fields && !ghost) {  // W, u, Q of this state, stored by the maxima pass
             const int c = cy * p.nx + cx;
             const long long P = p.plane;
 #pragma unroll
@@ -213,7 +251,7 @@ __global__ void __launch_bounds__(XW * RR, sizeof(S) == 4 ? 1024 / (XW * RR) : 5
     {
       const int r = F - RR + 1 + ty;
       const bool act = r >= y0 - H + 1 && r < yend + H - 1 && px >= x0 - H + 1 && px < xend + H - 1 &&
-                       !(zy && (r < 0 || r >= p.ny)) && !(zx && !x_in) && p.beta_mode == 0;
+                       !(zy && (r < 0 || r >= p.ny)) && !x_void && p.beta_mode == 0;
       if (act) {
         const int sm = ring<RQ>(r - 1, base), s0 = ring<RQ>(r, base), sp = ring<RQ>(r + 1, base);
         M qxp[4], qxm[4], qyp[4], qym[4];
@@ -269,7 +307,7 @@ __global__ void __launch_bounds__(XW * RR, sizeof(S) == 4 ? 1024 / (XW * RR) : 5
     {
       const int r = F - RR + ty;
       const bool act = r >= y0 - H + 2 && r < yend + H - 2 && px >= x0 - H + 2 && px < xend + H - 2 &&
-                       !(zy && (r < 0 || r >= p.ny)) && !(zx && !x_in);
+                       !(zy && (r < 0 || r >= p.ny)) && !x_void;
       if (act) {
         M beta = co.beta_const;
         if (p.beta_mode == 0) {
@@ -353,14 +391,14 @@ struct RollCfg {
 };
 
 constexpr int kMaxDevices = 64;
-int g_grid[kMaxDevices][4];  // persistent grid size per device and configuration (0: not set)
+int g_grid[kMaxDevices][8];  // persistent grid size per device and configuration (0: not set)
 
-template <class S, bool LOOK>
+template <class S, bool LOOK, bool INFLOW>
 constexpr int cfg_index() {
-  return (sizeof(S) == 8 ? 0 : 2) + (LOOK ? 1 : 0);
+  return (sizeof(S) == 8 ? 0 : 2) + (LOOK ? 1 : 0) + (INFLOW ? 4 : 0);
 }
 
-template <class S, bool LOOK>
+template <class S, bool LOOK, bool INFLOW>
 cudaError_t launch_roll_t(const Launch& L_, const void* fin, void* fout, int pulled, const void* invM) {
   using C = RollCfg<S, LOOK>;
   using G = RollGeom<S, LOOK, C::XW, C::RR>;
@@ -368,28 +406,35 @@ cudaError_t launch_roll_t(const Launch& L_, const void* fin, void* fout, int pul
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  const int grid = (dev >= 0 && dev < kMaxDevices) ? g_grid[dev][cfg_index<S, LOOK>()] : 0;
+  const int grid = (dev >= 0 && dev < kMaxDevices) ? g_grid[dev][cfg_index<S, LOOK, INFLOW>()] : 0;
   if (grid <= 0) return cudaErrorInitializationError;  // prepare_roll_kernels() not run on this device
-  k_roll<S, LOOK, C::XW, C::RR><<<grid, G::NT, G::smem_bytes, L_.stream>>>(
+  k_roll<S, LOOK, C::XW, C::RR, INFLOW><<<grid, G::NT, G::smem_bytes, L_.stream>>>(
       (const S*)fin, (S*)fout, L_.sc, p, pulled, (const typename Store<S>::M*)invM, L_.part,
       (!LOOK && sizeof(S) == 8) ? L_.fields : nullptr, (!LOOK && sizeof(S) == 8) ? L_.sens : nullptr);
   return cudaGetLastError();
 }
 
 // Opt-in shared memory, and the persistent grid: SMs x resident CTAs per SM.
-template <class S, bool LOOK>
+template <class S, bool LOOK, bool INFLOW>
 cudaError_t prepare_roll_t(int dev, int sms) {
   using C = RollCfg<S, LOOK>;
   using G = RollGeom<S, LOOK, C::XW, C::RR>;
-  cudaError_t e = cudaFuncSetAttribute(k_roll<S, LOOK, C::XW, C::RR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)G::smem_bytes);
+  cudaError_t e = cudaFuncSetAttribute(k_roll<S, LOOK, C::XW, C::RR, INFLOW>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_bytes);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_roll<S, LOOK, C::XW, C::RR>, G::NT, G::smem_bytes);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_roll<S, LOOK, C::XW, C::RR, INFLOW>, G::NT,
+                                                    G::smem_bytes);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  g_grid[dev][cfg_index<S, LOOK>()] = sms * per_sm;
+  g_grid[dev][cfg_index<S, LOOK, INFLOW>()] = sms * per_sm;
   return cudaSuccess;
+}
+
+template <class S, bool LOOK>
+cudaError_t prepare_roll_pair(int dev, int sms) {
+  cudaError_t e = prepare_roll_t<S, LOOK, false>(dev, sms);
+  return e == cudaSuccess ? prepare_roll_t<S, LOOK, true>(dev, sms) : e;
 }
 
 }  // namespace
@@ -400,10 +445,10 @@ cudaError_t prepare_roll_kernels() {
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  e = prepare_roll_t<double, false>(dev, sms);
-  if (e == cudaSuccess) e = prepare_roll_t<double, true>(dev, sms);
-  if (e == cudaSuccess) e = prepare_roll_t<float, false>(dev, sms);
-  if (e == cudaSuccess) e = prepare_roll_t<float, true>(dev, sms);
+  e = prepare_roll_pair<double, false>(dev, sms);
+  if (e == cudaSuccess) e = prepare_roll_pair<double, true>(dev, sms);
+  if (e == cudaSuccess) e = prepare_roll_pair<float, false>(dev, sms);
+  if (e == cudaSuccess) e = prepare_roll_pair<float, true>(dev, sms);
   return e;
 }
 
@@ -422,14 +467,21 @@ long long roll_ctas(const KParams& p) {
 
 cudaError_t launch_roll(const Launch& L, int precision, bool lookahead, const void* fin, void* fout, int pulled) {
   const char* base = reinterpret_cast<const char*>(L.sc);
+  const bool inflow = L.p->bc[0] == 2;
   if (precision == 0) {
     const void* invM = base + offsetof(Scalars, inv_M);
-    return lookahead ? launch_roll_t<double, true>(L, fin, fout, pulled, invM)
-                     : launch_roll_t<double, false>(L, fin, fout, pulled, invM);
+    if (inflow)
+      return lookahead ? launch_roll_t<double, true, true>(L, fin, fout, pulled, invM)
+                       : launch_roll_t<double, false, true>(L, fin, fout, pulled, invM);
+    return lookahead ? launch_roll_t<double, true, false>(L, fin, fout, pulled, invM)
+                     : launch_roll_t<double, false, false>(L, fin, fout, pulled, invM);
   }
   const void* invM = base + offsetof(Scalars, inv_M_f);
-  return lookahead ? launch_roll_t<float, true>(L, fin, fout, pulled, invM)
-                   : launch_roll_t<float, false>(L, fin, fout, pulled, invM);
+  if (inflow)
+    return lookahead ? launch_roll_t<float, true, true>(L, fin, fout, pulled, invM)
+                     : launch_roll_t<float, false, true>(L, fin, fout, pulled, invM);
+  return lookahead ? launch_roll_t<float, true, false>(L, fin, fout, pulled, invM)
+                   : launch_roll_t<float, false, false>(L, fin, fout, pulled, invM);
 }
 
 }  // namespace vlbm

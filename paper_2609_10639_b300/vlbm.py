@@ -17,7 +17,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libvlbm.so")
 
 OK, E_INVAL, E_NOMEM, E_CUDA, E_NONPHYSICAL, E_TIMEOUT, E_STATE, E_CHECKSUM, E_UNSUPPORTED = range(9)
-BC = {"periodic": 0, "zerograd": 1}
+BC = {"periodic": 0, "zerograd": 1, "inflow": 2}
 PRECISION = {"fp64": 0, "fp32_store": 1}
 ALGORITHM = {"auto": 0, "two_pass": 1, "lookahead": 2}
 TILING = {"auto": 0, "tile": 1, "strip": 2}
@@ -40,7 +40,7 @@ class _Grid(C.Structure):
 
 class _Eos(C.Structure):
     _fields_ = [("kind", C.c_int32), ("gamma", C.c_double), ("a", C.c_double), ("b", C.c_double), ("R", C.c_double),
-                ("cv", C.c_double)]
+                ("cv", C.c_double), ("cv1", C.c_double), ("cv2", C.c_double)]
 
 
 class _Params(C.Structure):
@@ -76,6 +76,7 @@ def _load():
         "vlbm_save_state": [V, V, C.c_size_t, C.POINTER(C.c_size_t)],
         "vlbm_load_state": [V, V, C.c_size_t],
         "vlbm_measure_fp64_peak": [I32, D],
+        "vlbm_set_inflow": [V, V],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -101,6 +102,14 @@ def _check(status: int, what: str):
     if status == E_NONPHYSICAL:
         raise NonPhysicalState(status, what)
     raise VLBMError(status, what)
+
+
+def _eos_struct(e: dict) -> "_Eos":
+    """vlbm_eos of an EOS description: ideal gas, van der Waals, or van der Waals with c_v(T)."""
+    if e["kind"] == "ideal":
+        return _Eos(0, e["gamma"], 0.0, 0.0, 0.0, 0.0, 0.0, 0.0)
+    kind = 2 if e["kind"] == "vdw_cvt" else 1
+    return _Eos(kind, 0.0, e["a"], e["b"], e["R"], e["cv"], e.get("cv1", 0.0), e.get("cv2", 0.0))
 
 
 def _ptr(a) -> int:
@@ -147,11 +156,7 @@ class Solver:
         self.device = torch.device("cuda", torch.cuda.current_device())
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         g = _Grid(cfg.dim, cfg.nx, self.ny, *[float(v) for v in cfg.extent], (C.c_int32 * 4)(*[BC[b] for b in cfg.bc]))
-        e = cfg.eos
-        if e["kind"] == "ideal":
-            eo = _Eos(0, e["gamma"], 0.0, 0.0, 0.0, 0.0)
-        else:
-            eo = _Eos(1, 0.0, e["a"], e["b"], e["R"], e["cv"])
+        eo = _eos_struct(cfg.eos)
         p = _Params(cfg.cfl, 0 if cfg.beta_mode == "sensor" else 1, cfg.beta_const, cfg.beta_min, cfg.beta_max,
                     cfg.c_sensor, cfg.ducros_eps, cfg.retarget_every, PRECISION[cfg.precision], ALGORITHM[cfg.algorithm],
                     TILING[cfg.tiling])
@@ -166,7 +171,17 @@ class Solver:
                   beta_min=prob.beta_min, beta_max=prob.beta_max, c_sensor=prob.c_sensor, ducros_eps=prob.ducros_eps,
                   precision=precision, algorithm=algorithm)
         kw.update(over)
-        return cls(Config(**kw), stream=stream)
+        s = cls(Config(**kw), stream=stream)
+        if "inflow" in prob.bc:
+            from . import workloads as wl
+
+            s.set_inflow(wl.inflow_state(prob))
+        return s
+
+    def set_inflow(self, W_in) -> None:
+        """State (D+2 conserved values) held by the ghost cells of the pinned-inflow x-lo side."""
+        w = np.ascontiguousarray(np.asarray(W_in, dtype=np.float64).reshape(-1))
+        _check(_lib.vlbm_set_inflow(self._h, C.c_void_p(w.ctypes.data)), "vlbm_set_inflow")
 
     def close(self):
         if getattr(self, "_h", None):
@@ -290,7 +305,7 @@ def _config_structs(cfg: Config):
     ny = 1 if cfg.dim == 1 else cfg.ny
     g = _Grid(cfg.dim, cfg.nx, ny, *[float(v) for v in cfg.extent], (C.c_int32 * 4)(*[BC[b] for b in cfg.bc]))
     e = cfg.eos
-    eo = _Eos(0, e["gamma"], 0.0, 0.0, 0.0, 0.0) if e["kind"] == "ideal" else _Eos(1, 0.0, e["a"], e["b"], e["R"], e["cv"])
+    eo = _eos_struct(e)
     p = _Params(cfg.cfl, 0 if cfg.beta_mode == "sensor" else 1, cfg.beta_const, cfg.beta_min, cfg.beta_max,
                 cfg.c_sensor, cfg.ducros_eps, cfg.retarget_every, PRECISION[cfg.precision], ALGORITHM[cfg.algorithm],
                     TILING[cfg.tiling])

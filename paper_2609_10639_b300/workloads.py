@@ -80,6 +80,10 @@ class Problem:
 IDEAL14 = {"kind": "ideal", "gamma": 1.4}
 # Reduced van der Waals units (rho_c = P_c = T_c = 1): a = 3, b = 1/3, R = 8/3, cv = 50 R.
 VDW_REDUCED = {"kind": "vdw", "a": 3.0, "b": 1.0 / 3.0, "R": 8.0 / 3.0, "cv": 50.0 * 8.0 / 3.0}
+# The same gas with a temperature-dependent heat capacity c_v(T) = R (40 + 8 T + 2 T^2) (50 R at the
+# critical temperature T = 1): a non-polytropic closure whose e -> T inversion needs Newton's method.
+VDW_CVT_REDUCED = {"kind": "vdw_cvt", "a": 3.0, "b": 1.0 / 3.0, "R": 8.0 / 3.0, "cv": 40.0 * 8.0 / 3.0,
+                   "cv1": 8.0 * 8.0 / 3.0, "cv2": 2.0 * 8.0 / 3.0}
 
 ZG = ("zerograd",) * 4
 PER = ("periodic",) * 4
@@ -87,6 +91,8 @@ PER = ("periodic",) * 4
 SOD_1D = Problem("sod_1d_1000", 1, 1000, 1, (0.0, 1.0, 0.0, 0.0), ZG, IDEAL14, 0.5, 0.2, 0)
 QUADRANTS_2D = Problem("quadrants_2d_4096", 2, 4096, 4096, (0.0, 1.0, 0.0, 1.0), ZG, IDEAL14, 0.5, 0.25, 0)
 BZT_2D = Problem("bzt_interface_2d_2048", 2, 2048, 2048, (0.0, 1.0, 0.0, 1.0), ZG, VDW_REDUCED, 0.5, 0.2, 0)
+# The BZT interface input with the non-polytropic gas (the same seeded states and perturbation).
+BZT_CVT_2D = Problem("bzt_interface_cvt_2d_2048", 2, 2048, 2048, (0.0, 1.0, 0.0, 1.0), ZG, VDW_CVT_REDUCED, 0.5, 0.2, 0)
 VORTEX_SCALE_2D = Problem("vortex_acoustic_2d_8192", 2, 8192, 8192, (0.0, 10.0, 0.0, 10.0), PER, IDEAL14, 0.5, 0.0, 2000)
 VORTEX_ADJOINT_2D = Problem("vortex_adjoint_2d_1024", 2, 1024, 1024, (0.0, 10.0, 0.0, 10.0), PER, IDEAL14, 0.5, 0.0, 1000)
 
@@ -111,7 +117,7 @@ SHOCK_VORTEX_IDEAL = Problem("shock_vortex_ideal_800x300", 2, 800, 300, (0.0, 16
 SHOCK_VORTEX_BZT = Problem("shock_vortex_bzt_1200x450", 2, 1200, 450, (0.0, 16.0, 0.0, 6.0), INFLOW_BC, BZT_SV_EOS,
                            0.5, 15.0, 0)
 
-PROBLEMS = {p.name: p for p in (SOD_1D, QUADRANTS_2D, BZT_2D, VORTEX_SCALE_2D, VORTEX_ADJOINT_2D, STRONG_SHOCK_1D,
+PROBLEMS = {p.name: p for p in (SOD_1D, QUADRANTS_2D, BZT_2D, BZT_CVT_2D, VORTEX_SCALE_2D, VORTEX_ADJOINT_2D, STRONG_SHOCK_1D,
                                 SHU_OSHER_1D, GRESHO_2D, SHOCK_VORTEX_IDEAL, SHOCK_VORTEX_BZT)}
 
 
@@ -131,10 +137,15 @@ def cell_centres(p: Problem):
 # (Eq. 15 ideal gas; Eqs. 16-17 van der Waals solved for T, then e = cv T - a rho).
 # ------------------------------------------------------------------------------------------
 def internal_energy(eos: dict, rho, P):
+    """e of (rho, P): ideal gas (Eq. 15); van der Waals T from Eq. (16), then e = cv T - a rho
+    (Eq. 17), or, for the temperature-dependent heat capacity c_v(T) = cv + cv1 T + cv2 T^2
+    ("vdw_cvt"), e = cv T + cv1 T^2/2 + cv2 T^3/3 - a rho."""
     if eos["kind"] == "ideal":
         return P / ((eos["gamma"] - 1.0) * rho)
     a, b, R, cv = eos["a"], eos["b"], eos["R"], eos["cv"]
     T = (P + a * rho * rho) * (1.0 - b * rho) / (R * rho)
+    if eos["kind"] == "vdw_cvt":
+        return cv * T + eos["cv1"] * T * T / 2.0 + eos["cv2"] * T * T * T / 3.0 - a * rho
     return cv * T - a * rho
 
 
@@ -468,7 +479,7 @@ def initial_field(p: Problem) -> np.ndarray:
         return gresho_2d(p)
     if base.startswith("quadrants_2d"):
         return quadrants_2d(p)
-    if base.startswith("bzt_interface_2d"):
+    if base.startswith("bzt_interface_2d") or base.startswith("bzt_interface_cvt_2d"):
         return bzt_interface_2d(p)
     if base.startswith("vortex_acoustic_2d"):
         return vortex_acoustic_2d(p)

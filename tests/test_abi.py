@@ -95,3 +95,17 @@ def test_noalloc_rejects_oversized_grids_without_touching_the_gpu():
     for nx, ny in ((2 ** 32, 2 ** 32), (2 ** 21 + 1, 1), (1, 2 ** 40), (2048, 1025)):
         g = vlbm._Grid(2, nx, ny, 0.0, 1.0, 0.0, 1.0, (C.c_int32 * 4)(1, 1, 1, 1))
         assert L.vlbm_beta_noalloc(C.byref(g), C.byref(e), C.byref(p), dummy, 1, dummy, None) == vlbm.E_INVAL
+
+
+def test_create_accepts_pinned_inflow_only_on_x_lo_with_an_outflow_partner():
+    # VLBM_BC_INFLOW (2): x-lo side only, paired with a zero-gradient x-hi side; checked on the host
+    from paper_2609_10639_b300 import vlbm
+
+    L = vlbm.library()
+    e = vlbm._Eos(0, 1.4, 0, 0, 0, 0)
+    p = vlbm._Params(0.5, 0, 1.0, 0.75, 1.0, 4.0, 1e-6, 1, 0, 0, 0)
+    h = C.c_void_p()
+    for bc in ((1, 2, 0, 0), (2, 0, 0, 0), (2, 2, 0, 0), (1, 1, 2, 1), (0, 0, 1, 2)):
+        g = vlbm._Grid(2, 16, 8, 0.0, 1.0, 0.0, 0.5, (C.c_int32 * 4)(*bc))
+        assert L.vlbm_create(C.byref(g), C.byref(e), C.byref(p), None, C.byref(h)) == vlbm.E_INVAL, bc
+    assert L.vlbm_set_inflow(None, None) == vlbm.E_INVAL
