@@ -48,11 +48,18 @@ struct RollGeom {
   // The y- ring is one row short of the others: 4 resident CTAs per SM in FP32.
   __host__ __device__ static constexpr int RF(int i) { return i == 2 ? RR + 1 : RR + 2; }
   __host__ __device__ static constexpr int OF(int i) { return i <= 2 ? i * (RR + 2) : 2 * (RR + 2) + RR + 1; }
+  // FP64 two-pass form: the x pass of the box filter runs once per row in a stage of its own (S2x)
+  // into a ring of x-filtered (s, theta) rows, instead of three times per cell in S3 (8 FP64
+  // operations per cell fewer on the FP64 pipe that bounds that kernel); the raw (s, theta) ring
+  // then only holds the RR rows S2 has just written.
+  static constexpr bool XF = sizeof(M) == 8 && !LOOK;
+  static constexpr int RSR = XF ? RR : RS;  // rows of the raw (s, theta) ring
   static constexpr size_t nQ = (size_t)RQ * 2 * XW * 4;
   static constexpr size_t nU = (size_t)RQ * XW * 2;
-  static constexpr size_t nS = (size_t)RS * XW * 2;
+  static constexpr size_t nS = (size_t)RSR * XW * 2;
   static constexpr size_t nF = LOOK ? (size_t)(OF(3) + RF(3)) * XW * 4 : 0;
-  static constexpr size_t smem_bytes = (nQ + nU + nS + nF) * sizeof(M);
+  static constexpr size_t nX = XF ? (size_t)RS * XW * 2 : 0;  // x-filtered (s, theta) ring
+  static constexpr size_t smem_bytes = (nQ + nU + nS + nF + nX) * sizeof(M);
   static_assert(RR >= 2, "stage S2 of a block reads u/Q one row beyond it");
 };
 
@@ -91,6 +98,7 @@ __global__ void __launch_bounds__(XW * RR, sizeof(S) == 4 ? 1024 / (XW * RR) : 5
   M* sU = sQ + G::nQ;                      // [RQ][XW][2]
   M* sS = sU + G::nU;                      // [RS][XW][2]
   M* sF = sS + G::nS;                      // direction i: [RF(i)][XW][4] from row OF(i) (look-ahead)
+  M* sX = sF + G::nF;                      // [RS][XW][2] x-filtered (s, theta) (FP64 two-pass)
 
   const Coef<M>& co = coef<M>(p);
   const int tx = threadIdx.x % XW, ty = threadIdx.x / XW;
@@ -293,7 +301,7 @@ __global__ void __launch_bounds__(XW * RR, sizeof(S) == 4 ? 1024 / (XW * RR) : 5
             sens[7 * P + c] = vt * p.inv2dx;
           }
         }
-        const int ss = ring<RS>(r, base);
+        const int ss = ring<G::RSR>(r, base);
         if constexpr (sizeof(M) == 8) {
           reinterpret_cast<double2*>(sS)[ss * XW + tx] = make_double2((double)sval, (double)th);
         } else {
@@ -303,6 +311,20 @@ __global__ void __launch_bounds__(XW * RR, sizeof(S) == 4 ? 1024 / (XW * RR) : 5
     }
     __syncthreads();
 
+    // ---- S2x (FP64 two-pass): x pass of the box filter of rows [F-RR+1, F+1) ----
+    if constexpr (G::XF) {
+      const int r = F - RR + 1 + ty;
+      const bool act = r >= y0 - H + 1 && r < yend + H - 1 && px >= x0 - H + 2 && px < xend + H - 2 &&
+                       !(zy && (r < 0 || r >= p.ny)) && !x_void && p.beta_mode == 0;
+      if (act) {
+        const double2* s2 = reinterpret_cast<const double2*>(sS) + ring<G::RSR>(r, base) * XW;
+        const double2 e0 = s2[xi(-1)], e1 = s2[tx], e2 = s2[xi(1)];
+        reinterpret_cast<double2*>(sX)[ring<RS>(r, base) * XW + tx] =
+            make_double2(box3(e0.x, e1.x, e2.x), box3(e0.y, e1.y, e2.y));
+      }
+      __syncthreads();
+    }
+
     // ---- S3: beta, fused reprojection + relaxation of rows [F-RR, F), single write ----
     {
       const int r = F - RR + ty;
@@ -310,7 +332,16 @@ __global__ void __launch_bounds__(XW * RR, sizeof(S) == 4 ? 1024 / (XW * RR) : 5
                        !(zy && (r < 0 || r >= p.ny)) && !x_void;
       if (act) {
         M beta = co.beta_const;
-        if (p.beta_mode == 0) {
+        if (p.beta_mode == 0 && G::XF) {
+          M rs[3], rt[3];
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            const double2 e = reinterpret_cast<const double2*>(sX)[ring<RS>(yc(r - 1 + j), base) * XW + tx];
+            rs[j] = (M)e.x;
+            rt[j] = (M)e.y;
+          }
+          beta = beta_of<M>(co, co.c_chi2 * box3(rs[0], rs[1], rs[2]) * box3(rt[0], rt[1], rt[2]));
+        } else if (p.beta_mode == 0) {
           const int xm = xi(-1), xp = xi(1);
           M rs[3], rt[3];
 #pragma unroll
