@@ -48,6 +48,11 @@ FP64_FLOPS_STEP_KERNEL = 178
 # Algorithmic bytes of one adjoint step including the recomputation of the forward state (FP64):
 # recompute 256 + read the forward state 128 + read lambda 128 + write lambda 128.
 ADJ_BYTES_PER_CELL = 640
+# FP64 floating-point operations per cell of one adjoint step (the reverse of one time step:
+# k_adj_local 237, k_adj_flux 153, k_adj_filter 82; FMA counted as 2), counted by ncu's executed
+# DADD/DMUL/DFMA thread instructions on the 1024^2 adjoint workload (profiles/adjoint_kernels_vortex_1024.md).
+# The paper gives no operation count for the adjoint; this is the executed arithmetic.
+ADJ_FLOPS_PER_CELL = 472
 FP64_FMA_PER_CLK_PER_SM = 2  # B300 FP64 unit count per SM (nominal figure, for context)
 
 
@@ -313,15 +318,17 @@ def cpu_baselines():
 
 
 def other_workloads(S, K, W, world):
-    """FP64 and FP32-storage throughput of the other workloads the library runs: the shock-vortex
-    interaction with its pinned-inflow boundary (ideal gas, 800 x 300) and the BZT interface input
-    with the non-polytropic gas (c_v(T), FP64 Newton inversion of e -> T; 2048^2)."""
+    """FP64 and FP32-storage throughput of the other workloads the library runs: the BZT interface
+    with the polytropic van der Waals gas (2048^2), the shock-vortex interaction with its
+    pinned-inflow boundary (ideal gas, 800 x 300) and the BZT interface input with the
+    non-polytropic gas (c_v(T), FP64 Newton inversion of e -> T; 2048^2)."""
     import torch
 
     from paper_2609_10639_b300 import workloads as wl
 
     out = {}
-    for prob, make in ((wl.SHOCK_VORTEX_IDEAL, wl.shock_vortex_2d), (wl.BZT_CVT_2D, wl.bzt_interface_2d)):
+    for prob, make in ((wl.BZT_2D, wl.bzt_interface_2d), (wl.SHOCK_VORTEX_IDEAL, wl.shock_vortex_2d),
+                       (wl.BZT_CVT_2D, wl.bzt_interface_2d)):
         W0 = torch.from_numpy(make(prob)).cuda()
         entry = {"grid": [prob.nx, prob.ny]}
         for prec in ("fp64", "fp32_store"):
@@ -466,7 +473,14 @@ def run_ours(args):
                 "recompute_ms": adj["rec_ms"],
                 "reverse_over_forward": adj["rev_ms"] / adj["fwd_ms"],
                 "adjoint_step_over_forward_step": (adj["rev_ms"] - adj["rec_ms"]) / adj["fwd_ms"],
-                "roofline": {"bound": "alu",
+                "roofline": {"bound": "alu", "unit": "TFLOP/s", "peak": fp64_peak,
+                             "achieved": ADJ_FLOPS_PER_CELL * adj["cells"] * adj["steps"]
+                                         / ((adj["rev_ms"] - adj["rec_ms"]) * 1e-3) / 1e12,
+                             "frac": ADJ_FLOPS_PER_CELL * adj["cells"] * adj["steps"]
+                                     / ((adj["rev_ms"] - adj["rec_ms"]) * 1e-3) / 1e12 / fp64_peak,
+                             "flops_per_cell": ADJ_FLOPS_PER_CELL,
+                             "kernels": "the adjoint-step kernels (k_adj_local, k_adj_flux, k_adj_filter and "
+                                        "the folds) over the reverse pass minus its segment recomputation",
                              "note": "every adjoint kernel is FP64-pipe bound (ncu: "
                                      "profiles/adjoint_kernels_vortex_1024.md)",
                              "hbm_achieved_gbs": ADJ_BYTES_PER_CELL * adj["cells"] * adj["steps"] / (adj["rev_ms"] * 1e-3) / 1e9,

@@ -43,6 +43,7 @@ struct vlbm_s {
   size_t scratch_elems = 0;
   double* fscratch = nullptr;  // populations readback (lazily allocated)
   double* fields = nullptr;    // FP64 strips: W, u, Q kept from the maxima pass (14 planes)
+  float* pkeep = nullptr;      // FP32 storage, look-ahead strips, non-ideal gas: kept pressure [2][plane]
   bool initialised = false;
   bool inflow_set = false;     // pinned-inflow grids: vlbm_set_inflow has supplied W_in
   bool unpulled = true;        // the current buffer holds equilibrium populations in place
@@ -99,6 +100,7 @@ vlbm::Launch launch_of(vlbm_t h, cudaStream_t s) {
   L.hist_c = h->hist_c;
   L.sched = h->sched;
   L.fields = h->fields;
+  L.pkeep = h->pkeep;
   return L;
 }
 
@@ -476,6 +478,9 @@ vlbm_status vlbm_create(const vlbm_grid* grid, const vlbm_eos* eos, const vlbm_p
   } else if (p.strip && h->precision == VLBM_FP64 &&
              cudaMalloc(&h->fields, (size_t)14 * p.plane * sizeof(double)) != cudaSuccess) {
     st = VLBM_E_NOMEM;
+  } else if (p.strip && h->precision == VLBM_FP32_STORE && h->lookahead && p.eos_kind != VLBM_EOS_IDEAL &&
+             cudaMalloc(&h->pkeep, (size_t)2 * p.plane * sizeof(float)) != cudaSuccess) {
+    st = VLBM_E_NOMEM;
   } else if (vlbm::prepare_kernels() != cudaSuccess) {
     st = VLBM_E_CUDA;
   }
@@ -511,6 +516,7 @@ vlbm_status vlbm_destroy(vlbm_t h) {
   cudaFree(h->scratch);
   cudaFree(h->fscratch);
   cudaFree(h->fields);
+  cudaFree(h->pkeep);
   cudaFree(h->adj.ckpt);
   cudaFree(h->adj.seg);
   cudaFree(h->adj.kept);
@@ -850,6 +856,8 @@ vlbm_status vlbm_load_state(vlbm_t h, const void* host, size_t n_bytes) {
   // saving handle had left in its own partials
   vlbm::Launch L = launch_of(h, h->stream);
   VLBM_TRY(vlbm::launch_reduce(L, h->precision, h->buf[cur], h->unpulled ? 0 : 1, false));
+  // the kept pressure of the restored state (FP32 look-ahead with a non-ideal gas)
+  VLBM_TRY(vlbm::launch_fill_pressure(L, h->buf[cur], h->unpulled ? 0 : 1));
   return sync_scalars(h);
 }
 

@@ -173,7 +173,8 @@ __device__ __forceinline__ void eos_eval(const KParams& p, const Coef<E>& c, E r
 // check (returns false for rho <= 0, c_s^2 <= 0 or non-finite values).  In the FP32 path the van
 // der Waals energy-to-temperature inversion and pressure run in FP64.
 template <int D, class M, bool NEED_CS>
-__device__ __forceinline__ bool prim_flux(const KParams& p, const M (&W)[D + 2], M (&u)[D], M (&Qf)[D][D + 2], M& cs) {
+__device__ __forceinline__ bool prim_flux(const KParams& p, const M (&W)[D + 2], M (&u)[D], M (&Qf)[D][D + 2], M& cs,
+                                          M* P_out = nullptr) {
   constexpr int NC = D + 2;
   const M rho = W[0];
   M P, cs2;
@@ -207,6 +208,7 @@ __device__ __forceinline__ bool prim_flux(const KParams& p, const M (&W)[D + 2],
     ok = (rho > (M)0) && (cs2 > (M)0) && isfinite(cs2) && isfinite(P);
     cs = sqrt_(cs2 > (M)0 ? cs2 : (M)0);
   }
+  if (P_out) *P_out = P;
 #pragma unroll
   for (int a = 0; a < D; ++a) {
     Qf[a][0] = W[1 + a];
@@ -215,6 +217,24 @@ __device__ __forceinline__ bool prim_flux(const KParams& p, const M (&W)[D + 2],
     Qf[a][NC - 1] = (W[NC - 1] + P) * u[a];
   }
   return ok;
+}
+
+// FP32 storage with a non-ideal gas: velocity and flux of W with the pressure P already known
+// (kept from the pass that computed it for the same W), the same operations as prim_flux's
+// non-ideal FP32 branch without the FP64 EOS evaluation, so the result is bit-identical.
+template <int D>
+__device__ __forceinline__ void flux_given_P(const float (&W)[D + 2], float P, float (&u)[D], float (&Qf)[D][D + 2]) {
+  constexpr int NC = D + 2;
+  const double ird = 1.0 / (double)W[0];
+#pragma unroll
+  for (int a = 0; a < D; ++a) u[a] = (float)((double)W[1 + a] * ird);
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    Qf[a][0] = W[1 + a];
+#pragma unroll
+    for (int b = 0; b < D; ++b) Qf[a][1 + b] = W[1 + b] * u[a] + (a == b ? P : 0.0f);
+    Qf[a][NC - 1] = (W[NC - 1] + P) * u[a];
+  }
 }
 
 // ------------------------------------------------------------------------------------------

@@ -100,6 +100,9 @@ struct Launch {
                              // and read by the step kernel (nullptr: not kept)
   double* sens = nullptr;    // FP64 two-pass strips, adjoint recomputation only: the step kernel
                              // also writes s_hat_0..3, s, theta, dil, vort of every cell (8 planes)
+  float* pkeep = nullptr;    // FP32 storage, look-ahead strips, non-ideal gas: pressure of the state
+                             // a step kernel starts from, [2][y][x] by step parity, written by the
+                             // pass that computed it for the same W (look-ahead stage, or init)
 };
 
 // precision: 0 = FP64, 1 = FP32 storage.  lookahead: fused single-kernel step.
@@ -121,6 +124,8 @@ cudaError_t prepare_kernels();
 // Column-strip form of the 2D step kernel (vlbm_roll.cu).
 cudaError_t launch_roll(const Launch& L, int precision, bool lookahead, const void* fin, void* fout, int pulled);
 cudaError_t prepare_roll_kernels();
+// Pressure of the current state into slot (n & 1) of L.pkeep (after a state restore).
+cudaError_t launch_fill_pressure(const Launch& L, const void* fin, int pulled);
 long long roll_ctas(const KParams& p);
 int sum_blocks(const KParams& p);
 int max_partials(const KParams& p);

@@ -44,11 +44,13 @@ namespace vlbm {
 // k_reduce: s_max and M_k of the current state (two-pass form; also feeds vlbm_get_beta)
 // ------------------------------------------------------------------------------------------
 // With `fields` (FP64, 2D) the pass also stores W, u and Q of every cell, so that the step
-// kernel reads them instead of recomputing moments, primitives and flux.
+// kernel reads them instead of recomputing moments, primitives and flux.  With `pk` it stores the
+// pressure of every cell into pk[n & 1] (the kept pressure the next FP32 look-ahead step reads;
+// used after a state restore).
 template <int D, class S, int NT>
 __global__ void __launch_bounds__(NT) k_reduce(const S* __restrict__ fin, Scalars* __restrict__ sc, const KParams p,
                                                 const int pulled, double* __restrict__ part, const int in_run,
-                                                double* __restrict__ fields) {
+                                                double* __restrict__ fields, float* __restrict__ pk) {
   using M = typename Store<S>::M;
   using R = Red<M>;
   constexpr int NC = D + 2;
@@ -73,7 +75,9 @@ __global__ void __launch_bounds__(NT) k_reduce(const S* __restrict__ fin, Scalar
     M fr[2 * D][NC], W[NC], u[D], Qf[D][NC], cs;
     load_cell<D, S>(fin, p, cx, cy, pulled, false, fr, inflow ? &gtab.f[0][0] : nullptr);
     moments<D, M, Store<S>::kOffset>(fr, wq, W);
-    bad |= !prim_flux<D, M, true>(p, W, u, Qf, cs);
+    M Pc;
+    bad |= !prim_flux<D, M, true>(p, W, u, Qf, cs, &Pc);
+    if (pk) pk[(long long)slot * p.plane + cell] = (float)Pc;
     cell_maxima<D, M>(u, cs, Qf, v);
     if constexpr (D == 2 && std::is_same<M, double>::value) {
       if (fields) {
@@ -528,7 +532,7 @@ __global__ void __launch_bounds__(kNTD) k_init_c0(Scalars* sc, const KParams p, 
 // partial slot 0.
 template <int D, class S, int NT>
 __global__ void __launch_bounds__(NT) k_init_eq(const double* __restrict__ W0, S* __restrict__ fout, Scalars* __restrict__ sc,
-                                                 const KParams p, double* __restrict__ part) {
+                                                 const KParams p, double* __restrict__ part, float* __restrict__ pk) {
   using M = typename Store<S>::M;
   using R = Red<M>;
   constexpr int NC = D + 2, Q = 2 * D;
@@ -540,6 +544,7 @@ __global__ void __launch_bounds__(NT) k_init_eq(const double* __restrict__ W0, S
   for (int k = 0; k < NC; ++k) wq[k] = Store<S>::kOffset ? (M)(Q * sc->wref[k]) : (M)0;
   bool bad = false;
   const double c0 = sc->c_prev;
+  static_assert(sizeof(S) == 4 || sizeof(S) == 8, "storage type");
   for (long long cell = (long long)blockIdx.x * NT + threadIdx.x; cell < p.plane; cell += (long long)gridDim.x * NT) {
     double W[NC], u[D], Qf[D][NC], cs;
 #pragma unroll
@@ -559,7 +564,9 @@ __global__ void __launch_bounds__(NT) k_init_eq(const double* __restrict__ W0, S
     store_cell<D, S, M>(fout, p, (int)cell, fr);
     M Ws[NC], us[D], Qs[D][NC], css;
     moments<D, M, Store<S>::kOffset>(fr, wq, Ws);
-    bad |= !prim_flux<D, M, true>(p, Ws, us, Qs, css);
+    M Pc;
+    bad |= !prim_flux<D, M, true>(p, Ws, us, Qs, css, &Pc);
+    if (pk) pk[cell] = (float)Pc;  // kept pressure of the state n = 0 (slot 0)
     cell_maxima<D, M>(us, css, Qs, v);
   }
   if (bad) atomicOr(&sc->err, ERR_NONPHYSICAL);
@@ -699,9 +706,9 @@ unsigned blocks_gs(const KParams& p) {
 }
 
 template <int D, class S>
-void launch_reduce_t(const Launch& L, const void* fin, int pulled, int in_run) {
+void launch_reduce_t(const Launch& L, const void* fin, int pulled, int in_run, float* pk = nullptr) {
   k_reduce<D, S, kNT1><<<blocks_gs(*L.p), kNT1, 0, L.stream>>>((const S*)fin, L.sc, *L.p, pulled, L.part, in_run,
-                                                                 in_run ? L.fields : nullptr);
+                                                                 in_run ? L.fields : nullptr, pk);
 }
 }  // namespace
 
@@ -744,6 +751,12 @@ cudaError_t launch_reduce(const Launch& L, int precision, const void* fin, int p
     if (precision == 0) launch_reduce_t<2, double>(L, fin, pulled, r);
     else launch_reduce_t<2, float>(L, fin, pulled, r);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill_pressure(const Launch& L, const void* fin, int pulled) {
+  if (!L.pkeep || L.p->dim != 2) return cudaSuccess;
+  launch_reduce_t<2, float>(L, fin, pulled, 0, L.pkeep);
   return cudaGetLastError();
 }
 
@@ -790,11 +803,11 @@ cudaError_t launch_init(const Launch& L, int precision, const double* W0, void* 
   }
   k_init_c0<<<1, kNTD, 0, L.stream>>>(L.sc, p, L.part, L.sched);
   if (p.dim == 1) {
-    if (precision == 0) k_init_eq<1, double, kNT1><<<blocks_gs(p), kNT1, 0, L.stream>>>(W0, (double*)fout, L.sc, p, L.part);
-    else k_init_eq<1, float, kNT1><<<blocks_gs(p), kNT1, 0, L.stream>>>(W0, (float*)fout, L.sc, p, L.part);
+    if (precision == 0) k_init_eq<1, double, kNT1><<<blocks_gs(p), kNT1, 0, L.stream>>>(W0, (double*)fout, L.sc, p, L.part, nullptr);
+    else k_init_eq<1, float, kNT1><<<blocks_gs(p), kNT1, 0, L.stream>>>(W0, (float*)fout, L.sc, p, L.part, nullptr);
   } else {
-    if (precision == 0) k_init_eq<2, double, kNT1><<<blocks_gs(p), kNT1, 0, L.stream>>>(W0, (double*)fout, L.sc, p, L.part);
-    else k_init_eq<2, float, kNT1><<<blocks_gs(p), kNT1, 0, L.stream>>>(W0, (float*)fout, L.sc, p, L.part);
+    if (precision == 0) k_init_eq<2, double, kNT1><<<blocks_gs(p), kNT1, 0, L.stream>>>(W0, (double*)fout, L.sc, p, L.part, nullptr);
+    else k_init_eq<2, float, kNT1><<<blocks_gs(p), kNT1, 0, L.stream>>>(W0, (float*)fout, L.sc, p, L.part, L.pkeep);
   }
   return cudaGetLastError();
 }
@@ -919,8 +932,8 @@ extern "C" vlbm_status vlbm_beta_noalloc(const vlbm_grid* grid, const vlbm_eos* 
   // The scalar block must start at zero (no error bit, step 0); the partials and 1/M_k are
   // fully written by this call before they are read.
   if (cudaMemsetAsync(sc, 0, sizeof(Scalars), s) != cudaSuccess) return VLBM_E_CUDA;
-  if (p.dim == 1) k_reduce<1, double, kNoallocCtaCells><<<ncta, kNoallocCtaCells, 0, s>>>(f, sc, p, pulled, part, 0, nullptr);
-  else k_reduce<2, double, kNoallocCtaCells><<<ncta, kNoallocCtaCells, 0, s>>>(f, sc, p, pulled, part, 0, nullptr);
+  if (p.dim == 1) k_reduce<1, double, kNoallocCtaCells><<<ncta, kNoallocCtaCells, 0, s>>>(f, sc, p, pulled, part, 0, nullptr, nullptr);
+  else k_reduce<2, double, kNoallocCtaCells><<<ncta, kNoallocCtaCells, 0, s>>>(f, sc, p, pulled, part, 0, nullptr, nullptr);
   k_beta_prep<<<1, kNTD, 0, s>>>(sc, p, part, invM);
   if (p.dim == 1) {
     constexpr int TX = TileCfg<1>::TX, TY = TileCfg<1>::TY;

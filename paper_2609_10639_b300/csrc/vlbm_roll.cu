@@ -80,13 +80,16 @@ __device__ __forceinline__ int ring(int r, int base) {
 // and runs two CTAs of up to 128 registers per SM, so that one CTA's stage S1 (loads only, with
 // W, u, Q kept by the maxima pass) overlaps the other's arithmetic.  INFLOW: the grid has a
 // pinned-inflow x-lo side (a separate instantiation: the ghost paths cost the FP32 kernel register
-// spills, 76 bytes, which the other grids need not pay).
-template <class S, bool LOOK, int XW, int RR, bool INFLOW>
+// spills, 76 bytes, which the other grids need not pay).  KEEP (FP32 storage, look-ahead, non-ideal
+// gas): stage S4 keeps the pressure it computes for the next state in pk[(n) & 1] and stage S1 reads
+// it from pk[(n - 1) & 1] instead of evaluating the FP64 equation of state a second time for the
+// same W (the FP64 EOS, with its Newton inversion for c_v(T), bounds that path); bit-identical.
+template <class S, bool LOOK, int XW, int RR, bool INFLOW, bool KEEP>
 __global__ void __launch_bounds__(XW * RR, sizeof(S) == 4 ? 1024 / (XW * RR) : 512 / (XW * RR)) k_roll(const S* __restrict__ fin, S* __restrict__ fout,
                                                   Scalars* __restrict__ sc, const KParams p, const int pulled,
                                                   const typename Store<S>::M* __restrict__ invM_src,
                                                   double* __restrict__ part, const double* __restrict__ fields,
-                                                  double* __restrict__ sens) {
+                                                  double* __restrict__ sens, float* __restrict__ pk) {
   using G = RollGeom<S, LOOK, XW, RR>;
   using M = typename G::M;
   constexpr int H = G::H, TXO = G::TXO, RQ = G::RQ, RS = G::RS;
@@ -123,6 +126,9 @@ __global__ void __launch_bounds__(XW * RR, sizeof(S) == 4 ? 1024 / (XW * RR) : 5
   }
   const M r_c = StepScalars<M>::r(sc), inv_c = StepScalars<M>::inv_c(sc);
   const int slot_n = (int)(sc->n & 1);
+  static_assert(!KEEP || (sizeof(S) == 4 && LOOK), "kept pressure: FP32 storage, look-ahead form only");
+  const float* pk_in = KEEP ? pk + (long long)(slot_n ^ 1) * p.plane : nullptr;  // written by the previous step
+  float* pk_out = KEEP ? pk + (long long)slot_n * p.plane : nullptr;
   // pinned inflow: the ghost values at the link speed of the stored populations, c_new r (read
   // after the barrier at the start of the first segment)
   __shared__ GhostTab<2, M> gtab;
@@ -173,6 +179,28 @@ __global__ void __launch_bounds__(XW * RR, sizeof(S) == 4 ? 1024 / (XW * RR) : 5
   };
   // positions beyond a zero-gradient x side hold no values of their own (reads land on the edge)
   const bool x_void = (zxl && px < 0) || (zxh && px >= p.nx);
+  // S4 (look-ahead) of block Fb: W^{n+1} of rows [Fb-RR-1, Fb-1) from the rings of relaxed
+  // populations and the next step's maxima.  It runs after a barrier at the end of its block, when
+  // only the populations carried to the next block are live (run alongside the next block's S2,
+  // which would save that barrier, it kept both blocks' populations live and spilled registers).
+  auto s4 = [&](int Fb) {
+    const int r = Fb - RR - 1 + ty;
+    if (r >= y0 && r < yend && px >= x0 && px < xend) {
+      M fr[4][4], W[4];
+      const int xm = xi(-1), xp = xi(1);
+      const int sfy = ring<G::RF(0)>(r, base);
+      const int sfm = ring<G::RF(3)>(yc(r - 1), base), sfp = ring<G::RF(2)>(yc(r + 1), base);
+      ld4s(sF + ((G::OF(0) + sfy) * XW + xp) * 4, fr[0]);  // f*_{x-} from x+1
+      ld4s(sF + ((G::OF(1) + sfy) * XW + xm) * 4, fr[1]);  // f*_{x+} from x-1
+      ld4s(sF + ((G::OF(2) + sfp) * XW + tx) * 4, fr[2]);  // f*_{y-} from y+1
+      ld4s(sF + ((G::OF(3) + sfm) * XW + tx) * 4, fr[3]);  // f*_{y+} from y-1
+      moments<2, M, OFF>(fr, wq, W);
+      M u[2], Qf[2][4], cs, Pc;
+      bad |= !prim_flux<2, M, true>(p, W, u, Qf, cs, KEEP ? &Pc : nullptr);
+      if constexpr (KEEP) pk_out[r * p.nx + px] = (float)Pc;
+      cell_maxima<2, M>(u, cs, Qf, vmax);
+    }
+  };
   __syncthreads();  // the rings of a previous segment are no longer read
 
   for (int F = base; F - RR - (LOOK ? 1 : 0) < yend; F += RR) {
@@ -241,7 +269,11 @@ __global__ void __launch_bounds__(XW * RR, sizeof(S) == 4 ? 1024 / (XW * RR) : 5
         }
         if (!have) {
           moments<2, M, OFF>(fnew, wq, W);
-          prim_flux<2, M, false>(p, W, u, Qf, cs);
+          if constexpr (KEEP) {
+            flux_given_P<2>(W, pk_in[cy * p.nx + cx], u, Qf);
+          } else {
+            prim_flux<2, M, false>(p, W, u, Qf, cs);
+          }
         }
         const int s = ring<RQ>(r, base);
 #pragma unroll
@@ -382,24 +414,9 @@ __global__ void __launch_bounds__(XW * RR, sizeof(S) == 4 ? 1024 / (XW * RR) : 5
 #pragma unroll
       for (int k = 0; k < 4; ++k) fcar[i][k] = fnew[i][k];
 
-    // ---- S4: W^{n+1} of rows [F-RR-1, F-1) and the next step's maxima ----
     if constexpr (LOOK) {
       __syncthreads();
-      const int r = F - RR - 1 + ty;
-      if (r >= y0 && r < yend && px >= x0 && px < xend) {
-        M fr[4][4], W[4];
-        const int xm = xi(-1), xp = xi(1);
-        const int sfy = ring<G::RF(0)>(r, base);
-        const int sfm = ring<G::RF(3)>(yc(r - 1), base), sfp = ring<G::RF(2)>(yc(r + 1), base);
-        ld4s(sF + ((G::OF(0) + sfy) * XW + xp) * 4, fr[0]);  // f*_{x-} from x+1
-        ld4s(sF + ((G::OF(1) + sfy) * XW + xm) * 4, fr[1]);  // f*_{x+} from x-1
-        ld4s(sF + ((G::OF(2) + sfp) * XW + tx) * 4, fr[2]);  // f*_{y-} from y+1
-        ld4s(sF + ((G::OF(3) + sfm) * XW + tx) * 4, fr[3]);  // f*_{y+} from y-1
-        moments<2, M, OFF>(fr, wq, W);
-        M u[2], Qf[2][4], cs;
-        bad |= !prim_flux<2, M, true>(p, W, u, Qf, cs);
-        cell_maxima<2, M>(u, cs, Qf, vmax);
-      }
+      s4(F);
     }
   }
   }  // segments
@@ -422,14 +439,14 @@ struct RollCfg {
 };
 
 constexpr int kMaxDevices = 64;
-int g_grid[kMaxDevices][8];  // persistent grid size per device and configuration (0: not set)
+int g_grid[kMaxDevices][16];  // persistent grid size per device and configuration (0: not set)
 
-template <class S, bool LOOK, bool INFLOW>
+template <class S, bool LOOK, bool INFLOW, bool KEEP>
 constexpr int cfg_index() {
-  return (sizeof(S) == 8 ? 0 : 2) + (LOOK ? 1 : 0) + (INFLOW ? 4 : 0);
+  return (sizeof(S) == 8 ? 0 : 2) + (LOOK ? 1 : 0) + (INFLOW ? 4 : 0) + (KEEP ? 8 : 0);
 }
 
-template <class S, bool LOOK, bool INFLOW>
+template <class S, bool LOOK, bool INFLOW, bool KEEP = false>
 cudaError_t launch_roll_t(const Launch& L_, const void* fin, void* fout, int pulled, const void* invM) {
   using C = RollCfg<S, LOOK>;
   using G = RollGeom<S, LOOK, C::XW, C::RR>;
@@ -437,35 +454,41 @@ cudaError_t launch_roll_t(const Launch& L_, const void* fin, void* fout, int pul
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  const int grid = (dev >= 0 && dev < kMaxDevices) ? g_grid[dev][cfg_index<S, LOOK, INFLOW>()] : 0;
+  const int grid = (dev >= 0 && dev < kMaxDevices) ? g_grid[dev][cfg_index<S, LOOK, INFLOW, KEEP>()] : 0;
   if (grid <= 0) return cudaErrorInitializationError;  // prepare_roll_kernels() not run on this device
-  k_roll<S, LOOK, C::XW, C::RR, INFLOW><<<grid, G::NT, G::smem_bytes, L_.stream>>>(
+  k_roll<S, LOOK, C::XW, C::RR, INFLOW, KEEP><<<grid, G::NT, G::smem_bytes, L_.stream>>>(
       (const S*)fin, (S*)fout, L_.sc, p, pulled, (const typename Store<S>::M*)invM, L_.part,
-      (!LOOK && sizeof(S) == 8) ? L_.fields : nullptr, (!LOOK && sizeof(S) == 8) ? L_.sens : nullptr);
+      (!LOOK && sizeof(S) == 8) ? L_.fields : nullptr, (!LOOK && sizeof(S) == 8) ? L_.sens : nullptr,
+      KEEP ? L_.pkeep : nullptr);
   return cudaGetLastError();
 }
 
 // Opt-in shared memory, and the persistent grid: SMs x resident CTAs per SM.
-template <class S, bool LOOK, bool INFLOW>
+template <class S, bool LOOK, bool INFLOW, bool KEEP>
 cudaError_t prepare_roll_t(int dev, int sms) {
   using C = RollCfg<S, LOOK>;
   using G = RollGeom<S, LOOK, C::XW, C::RR>;
-  cudaError_t e = cudaFuncSetAttribute(k_roll<S, LOOK, C::XW, C::RR, INFLOW>,
+  cudaError_t e = cudaFuncSetAttribute(k_roll<S, LOOK, C::XW, C::RR, INFLOW, KEEP>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_bytes);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_roll<S, LOOK, C::XW, C::RR, INFLOW>, G::NT,
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_roll<S, LOOK, C::XW, C::RR, INFLOW, KEEP>, G::NT,
                                                     G::smem_bytes);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  g_grid[dev][cfg_index<S, LOOK, INFLOW>()] = sms * per_sm;
+  g_grid[dev][cfg_index<S, LOOK, INFLOW, KEEP>()] = sms * per_sm;
   return cudaSuccess;
 }
 
 template <class S, bool LOOK>
 cudaError_t prepare_roll_pair(int dev, int sms) {
-  cudaError_t e = prepare_roll_t<S, LOOK, false>(dev, sms);
-  return e == cudaSuccess ? prepare_roll_t<S, LOOK, true>(dev, sms) : e;
+  cudaError_t e = prepare_roll_t<S, LOOK, false, false>(dev, sms);
+  if (e == cudaSuccess) e = prepare_roll_t<S, LOOK, true, false>(dev, sms);
+  if constexpr (sizeof(S) == 4 && LOOK) {
+    if (e == cudaSuccess) e = prepare_roll_t<S, LOOK, false, true>(dev, sms);
+    if (e == cudaSuccess) e = prepare_roll_t<S, LOOK, true, true>(dev, sms);
+  }
+  return e;
 }
 
 }  // namespace
@@ -508,6 +531,9 @@ cudaError_t launch_roll(const Launch& L, int precision, bool lookahead, const vo
                      : launch_roll_t<double, false, false>(L, fin, fout, pulled, invM);
   }
   const void* invM = base + offsetof(Scalars, inv_M_f);
+  if (lookahead && L.pkeep && L.p->eos_kind != 0)  // non-ideal gas: pressure kept between the stages
+    return inflow ? launch_roll_t<float, true, true, true>(L, fin, fout, pulled, invM)
+                  : launch_roll_t<float, true, false, true>(L, fin, fout, pulled, invM);
   if (inflow)
     return lookahead ? launch_roll_t<float, true, true>(L, fin, fout, pulled, invM)
                      : launch_roll_t<float, false, true>(L, fin, fout, pulled, invM);

@@ -54,13 +54,20 @@ def test_totals_compensated_and_conserved(precision):
 @pytest.mark.parametrize("precision,algorithm", [("fp64", "two_pass"), ("fp64", "lookahead"),
                                                  ("fp32_store", "two_pass"), ("fp32_store", "lookahead")])
 @pytest.mark.parametrize("n_save", [0, 37])
-def test_save_load_resumes_bit_for_bit(precision, algorithm, n_save):
+@pytest.mark.parametrize("gas", ["ideal", "vdw"])
+def test_save_load_resumes_bit_for_bit(precision, algorithm, n_save, gas):
+    # the van der Waals FP32 look-ahead path keeps the pressure between the steps; a restored state
+    # recomputes it
     import torch
 
     from paper_2609_10639_b300 import vlbm
 
-    prob = wl.QUADRANTS_2D.resized(90, 70)
-    W0 = torch.from_numpy(wl.quadrants_2d(prob)).cuda()
+    if gas == "ideal":
+        prob = wl.QUADRANTS_2D.resized(90, 70)
+        W0 = torch.from_numpy(wl.quadrants_2d(prob)).cuda()
+    else:
+        prob = wl.BZT_2D.resized(90, 70)
+        W0 = torch.from_numpy(wl.bzt_interface_2d(prob)).cuda()
     a = vlbm.Solver.for_problem(prob, precision=precision, algorithm=algorithm)
     a.init(W0)
     if n_save:
@@ -104,3 +111,27 @@ def test_load_rejects_damaged_and_mismatched_states():
         assert e.value.status == vlbm.E_INVAL
     b.load_state(bytes(blob))
     assert b.time()[1] == 5
+
+
+@pytest.mark.parametrize("eos", ["vdw", "vdw_cvt"])
+def test_kept_pressure_is_bit_identical_to_the_eos_evaluation(eos):
+    # FP32 storage with a non-ideal gas: the strip kernel's look-ahead stage keeps the pressure of
+    # the next state for the next step (no second FP64 EOS evaluation); the tile kernel evaluates the
+    # EOS in both places.  The same operations on the same W: the runs agree to rounding (the two
+    # kernels may contract multiply-adds differently); a pressure taken from the wrong step or
+    # cell would differ by the change of a step, about 1e-3.
+    import torch
+
+    from paper_2609_10639_b300 import vlbm
+
+    prob = (wl.BZT_2D if eos == "vdw" else wl.BZT_CVT_2D).resized(200, 130)
+    W0 = torch.from_numpy(wl.bzt_interface_2d(prob)).cuda()
+    out = []
+    for tiling in ("strip", "tile"):
+        g = vlbm.Solver.for_problem(prob, precision="fp32_store", algorithm="lookahead", tiling=tiling)
+        g.init(W0)
+        assert g.step(70) == 70
+        out.append(g.W().cpu().numpy())
+    rel = np.abs(out[0] - out[1]).reshape(4, -1).sum(1) / np.abs(out[1]).reshape(4, -1).sum(1)
+    print(f"{eos}: kept pressure (strips) against the EOS evaluation (tiles), relative L1 {rel}")
+    assert rel[[0, 3]].max() <= 1e-6
