@@ -159,3 +159,31 @@ def test_pinned_inflow_needs_its_state_and_has_no_adjoint():
     with pytest.raises(vlbm.VLBMError) as ei:
         s.adjoint(W0, 4, 2, torch.zeros_like(W0))
     assert ei.value.status == vlbm.E_UNSUPPORTED
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (2, 3), (5, 1), (1, 7), (131, 57)])
+@pytest.mark.parametrize("tiling", ["strip", "tile"])
+def test_pinned_inflow_on_degenerate_and_ragged_grids(shape, tiling):
+    # tiny and ragged grids with a pinned-inflow x-lo side: every cell next to the ghost column,
+    # strips narrower than the halo, a single row, against the oracle after 25 steps (FP64, both forms)
+    import torch
+
+    from oracle import oracle as O
+    from paper_2609_10639_b300 import vlbm
+
+    nx, ny = shape
+    prob = wl.Problem("inflow_small", 2, nx, ny, (0.0, 1.0, 0.0, ny / nx), wl.INFLOW_BC, wl.IDEAL14, 0.5, 0.0, 0)
+    X, Y = wl.cell_centres(prob)
+    rho = 1.0 + 0.2 * np.cos(2 * np.pi * Y) + 0.1 * X
+    W0 = wl.conserved(prob.eos, rho, [1.1 + 0 * X, 0.1 * np.sin(2 * np.pi * Y)], 1.0 + 0.1 * X)
+    W_in = wl.conserved(prob.eos, np.array(0.9), [np.array(1.3), np.array(0.0)], np.array(1.2)).reshape(-1)
+    for algorithm in ("two_pass", "lookahead"):
+        g = vlbm.Solver.for_problem(prob, algorithm=algorithm, tiling=tiling)
+        g.set_inflow(W_in)
+        g.init(torch.from_numpy(W0).cuda())
+        assert g.step(25) == 25
+        o = O.OracleSolver.for_problem(prob, threads=1)
+        o.set_inflow(W_in)
+        o.init(W0)
+        o.step(25)
+        assert rel_maxnorm(g.W().cpu().numpy(), o.W()) <= TOL, (shape, tiling, algorithm)
