@@ -186,4 +186,9 @@ def test_pinned_inflow_on_degenerate_and_ragged_grids(shape, tiling):
         o.set_inflow(W_in)
         o.init(W0)
         o.step(25)
-        assert rel_maxnorm(g.W().cpu().numpy(), o.W()) <= TOL, (shape, tiling, algorithm)
+        Wg, Wo = g.W().cpu().numpy(), o.W()
+        # per component, relative to its magnitude, or to 1e-3 of the state's where a component is
+        # at rounding level (one column fed by the pinned state: rho v ~ 1e-16 after 25 steps)
+        scale = np.maximum(np.abs(Wo).reshape(4, -1).max(1), 1e-3 * np.abs(Wo).max())
+        err = float((np.abs(Wg - Wo).reshape(4, -1).max(1) / scale).max())
+        assert err <= TOL, (shape, tiling, algorithm, err)
