@@ -669,8 +669,9 @@ struct TileCfg<2> {  // 2D tiles of 32 x 16 cells
   static constexpr int TX = 32, TY = 16;
 };
 template <>
-struct TileCfg<1> {  // 1D tiles of 256 cells
-  static constexpr int TX = 256, TY = 1;
+struct TileCfg<1> {  // 1D tiles of 64 cells: a 1000-cell problem spreads over 16 SMs (its FP64 work
+                     // took 4 SMs 12 us per step with 256-cell tiles)
+  static constexpr int TX = 64, TY = 1;
 };
 
 template <int D, class S, bool LOOK, bool BOUT>
@@ -707,8 +708,14 @@ unsigned blocks_gs(const KParams& p) {
 
 template <int D, class S>
 void launch_reduce_t(const Launch& L, const void* fin, int pulled, int in_run, float* pk = nullptr) {
-  k_reduce<D, S, kNT1><<<blocks_gs(*L.p), kNT1, 0, L.stream>>>((const S*)fin, L.sc, *L.p, pulled, L.part, in_run,
-                                                                 in_run ? L.fields : nullptr, pk);
+  if constexpr (D == 1) {  // CTAs of 64 cells, as the 1D tiles: the small 1D problems spread over more SMs
+    const long long b = (L.p->plane + 63) / 64;
+    k_reduce<D, S, 64><<<(unsigned)(b < kGridStride ? b : kGridStride), 64, 0, L.stream>>>(
+        (const S*)fin, L.sc, *L.p, pulled, L.part, in_run, nullptr, pk);
+  } else {
+    k_reduce<D, S, kNT1><<<blocks_gs(*L.p), kNT1, 0, L.stream>>>((const S*)fin, L.sc, *L.p, pulled, L.part, in_run,
+                                                                   in_run ? L.fields : nullptr, pk);
+  }
 }
 }  // namespace
 
