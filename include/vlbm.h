@@ -85,9 +85,10 @@ typedef enum { VLBM_FP64 = 0, VLBM_FP32_STORE = 1 } vlbm_precision;
 typedef enum { VLBM_BETA_SENSOR = 0, VLBM_BETA_CONST = 1 } vlbm_beta_mode;
 typedef enum { VLBM_ALGO_AUTO = 0, VLBM_ALGO_TWO_PASS = 1, VLBM_ALGO_LOOKAHEAD = 2 } vlbm_algorithm;
 /* How a 2D step kernel covers the grid: VLBM_TILING_STRIP walks a CTA down a column strip with
- * ring buffers (each quantity computed once per row; AUTO in 2D), VLBM_TILING_TILE computes each
- * 32 x 16 tile with its own halo.  Both give the same results up to rounding order; 1D always
- * uses tiles.  VLBM_ALGO_AUTO takes the look-ahead form for FP32 storage and the two-pass form
+ * ring buffers (each quantity computed once per row), VLBM_TILING_TILE computes each 32 x 16 tile
+ * with its own halo.  AUTO takes strips in 2D, except tiles for FP32 storage with an ideal gas on
+ * grids of fewer than 2^19 cells (measured faster there).  Both give the same results up to
+ * rounding order; 1D always uses tiles.  VLBM_ALGO_AUTO takes the look-ahead form for FP32 storage and the two-pass form
  * for FP64. */
 typedef enum { VLBM_TILING_AUTO = 0, VLBM_TILING_TILE = 1, VLBM_TILING_STRIP = 2 } vlbm_tiling;
 

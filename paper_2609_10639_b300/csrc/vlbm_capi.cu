@@ -365,10 +365,16 @@ void make_kparams(const vlbm_grid* grid, const vlbm_eos* eos, const vlbm_params*
   p.c_sensor = params->c_sensor;
   p.ducros_eps = params->ducros_eps;
   p.retarget_every = params->retarget_every;
-  // Column strips in 2D (each quantity computed once per row).  Measured on a B300 at 4096^2
-  // (per step, 1 GPU): FP64 strips 8.0 ms vs tiles 8.9 ms; FP32 storage strips 0.59 ms
-  // (look-ahead) vs tiles 0.73 ms (two-pass).
-  p.strip = (grid->dim == 2 && params->tiling != VLBM_TILING_TILE) ? 1 : 0;
+  // Column strips in 2D (each quantity computed once per row).  Measured on a B300 (per step):
+  // FP64 strips beat tiles on every grid tried (4096^2: 6.7 vs 8.9 ms; 800 x 300: 148 vs 200 us); in
+  // FP32 storage strips win on large grids (1024^2: 51 vs 63 us) and tiles on small ones with an
+  // ideal gas, where a strip segment is only a few rows long and its halo rows weigh (800 x 300:
+  // 25 vs 33 us, 512^2: 22 vs 28 us); with a non-ideal gas the strips keep the pressure between the
+  // stages and win (1200 x 450: 113 vs 153 us).
+  const long long cells = (long long)grid->nx * (grid->dim == 1 ? 1 : grid->ny);
+  const bool small_fp32_ideal = params->precision == VLBM_FP32_STORE && eos->kind == VLBM_EOS_IDEAL && cells < (1LL << 19);
+  p.strip = (grid->dim == 2 && (params->tiling == VLBM_TILING_STRIP ||
+                                (params->tiling == VLBM_TILING_AUTO && !small_fp32_ideal))) ? 1 : 0;
   Coef<double>& c = p.cd;
   c.gamma = p.gamma;
   c.gm1 = p.gamma - 1.0;
