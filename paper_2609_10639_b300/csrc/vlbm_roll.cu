@@ -179,13 +179,19 @@ __global__ void __launch_bounds__(XW * RR, sizeof(S) == 4 ? 1024 / (XW * RR) : 5
   };
   // positions beyond a zero-gradient x side hold no values of their own (reads land on the edge)
   const bool x_void = (zxl && px < 0) || (zxh && px >= p.nx);
+  // the column and row-range predicates of the stages, constant over the segment
+  const bool c1 = px >= x0 - H && px < xend + H;
+  const bool c2 = px >= x0 - H + 1 && px < xend + H - 1 && !x_void && p.beta_mode == 0;
+  const bool c3 = px >= x0 - H + 2 && px < xend + H - 2 && !x_void;
+  const bool cout = px >= x0 && px < xend;
+  const int r1hi = yend + H, r2lo = y0 - H + 1, r2hi = yend + H - 1, r3lo = y0 - H + 2, r3hi = yend + H - 2;
   // S4 (look-ahead) of block Fb: W^{n+1} of rows [Fb-RR-1, Fb-1) from the rings of relaxed
   // populations and the next step's maxima.  It runs after a barrier at the end of its block, when
   // only the populations carried to the next block are live (run alongside the next block's S2,
   // which would save that barrier, it kept both blocks' populations live and spilled registers).
   auto s4 = [&](int Fb) {
     const int r = Fb - RR - 1 + ty;
-    if (r >= y0 && r < yend && px >= x0 && px < xend) {
+    if (cout && r >= y0 && r < yend) {
       M fr[4][4], W[4];
       const int xm = xi(-1), xp = xi(1);
       const int sfy = ring<G::RF(0)>(r, base);
@@ -229,9 +235,9 @@ __global__ void __launch_bounds__(XW * RR, sizeof(S) == 4 ? 1024 / (XW * RR) : 5
     M fnew[4][4];
     {
       const int r = F + ty;
-      const bool act = r < yend + H && px >= x0 - H && px < xend + H;
+      const bool act = c1 && r < r1hi;
       if (act) {
-        const int cy = nb_index(r, p.ny, p.bc[2], p.bc[3]);
+        const int cy = (r >= 0 && r < p.ny) ? r : nb_index(r, p.ny, p.bc[2], p.bc[3]);
         const int cx = xedge ? nb_index(px, p.nx, p.bc[0], p.bc[1]) : px;
         const bool inner = !xedge && cy >= 1 && cy < p.ny - 1;
         const bool ghost = gx && px < 0;  // a ghost cell of the pinned-inflow side
@@ -294,8 +300,7 @@ __global__ void __launch_bounds__(XW * RR, sizeof(S) == 4 ? 1024 / (XW * RR) : 5
     // ---- S2: s and theta of rows [F-RR+1, F+1) ----
     {
       const int r = F - RR + 1 + ty;
-      const bool act = r >= y0 - H + 1 && r < yend + H - 1 && px >= x0 - H + 1 && px < xend + H - 1 &&
-                       !(zy && (r < 0 || r >= p.ny)) && !x_void && p.beta_mode == 0;
+      const bool act = c2 && r >= r2lo && r < r2hi && !(zy && (r < 0 || r >= p.ny));
       if (act) {
         const int sm = ring<RQ>(r - 1, base), s0 = ring<RQ>(r, base), sp = ring<RQ>(r + 1, base);
         M qxp[4], qxm[4], qyp[4], qym[4];
@@ -364,8 +369,7 @@ __global__ void __launch_bounds__(XW * RR, sizeof(S) == 4 ? 1024 / (XW * RR) : 5
     // ---- S3: beta, fused reprojection + relaxation of rows [F-RR, F), single write ----
     {
       const int r = F - RR + ty;
-      const bool act = r >= y0 - H + 2 && r < yend + H - 2 && px >= x0 - H + 2 && px < xend + H - 2 &&
-                       !(zy && (r < 0 || r >= p.ny)) && !x_void;
+      const bool act = c3 && r >= r3lo && r < r3hi && !(zy && (r < 0 || r >= p.ny));
       if (act) {
         M beta = co.beta_const;
         if (p.beta_mode == 0 && G::XF) {
@@ -403,7 +407,7 @@ __global__ void __launch_bounds__(XW * RR, sizeof(S) == 4 ? 1024 / (XW * RR) : 5
         ld4s(sQ + ((sq * 2 + 0) * XW + tx) * 4, Qc[0]);
         ld4s(sQ + ((sq * 2 + 1) * XW + tx) * 4, Qc[1]);
         relax_cell<2, M>(fcar, Qc, beta, r_c, inv_c);
-        if (r >= y0 && r < yend && px >= x0 && px < xend) store_cell<2, S, M>(fout, p, r * p.nx + px, fcar);
+        if (cout && r >= y0 && r < yend) store_cell<2, S, M>(fout, p, r * p.nx + px, fcar);
         if constexpr (LOOK) {
           const int s4 = ring<G::RF(0)>(r, base), s3 = ring<G::RF(2)>(r, base);
           st4s(sF + ((G::OF(0) + s4) * XW + tx) * 4, fcar[0]);

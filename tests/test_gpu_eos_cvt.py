@@ -139,6 +139,6 @@ def test_cvt_on_degenerate_and_ragged_grids(shape, precision):
         g64 = vlbm.Solver.for_problem(prob)
         g64.init(torch.from_numpy(W0).cuda())
         g64.step(25)
-        W32, W64 = g.W().cpu().numpy(), g64.W().cpu().numpy()
-        rel = np.abs(W32 - W64).reshape(4, -1).sum(1) / np.abs(W64).reshape(4, -1).sum(1)
-        assert rel[[0, 3]].max() <= 1e-5
+        W32, W64 = g.W().cpu().numpy()[[0, 3]], g64.W().cpu().numpy()[[0, 3]]  # rho, rho E
+        rel = np.abs(W32 - W64).reshape(2, -1).sum(1) / np.abs(W64).reshape(2, -1).sum(1)
+        assert rel.max() <= 1e-5
