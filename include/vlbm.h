@@ -145,6 +145,21 @@ vlbm_status vlbm_step(vlbm_t h, int64_t n_steps, double t_end, int64_t* steps_do
 /* W = sum_i f_i of the current state (Sec. III A), (D+2) * ny * nx float64 values. */
 vlbm_status vlbm_get_W(vlbm_t h, double* W);
 
+/* n_runs independent runs on this handle's grid, gas and parameters, one after another: run k is
+ * vlbm_init(W0s[k]), vlbm_step(n_steps, t_end) and vlbm_get_W(Ws[k]), with the same results.
+ * W0s[k], Ws[k]: (D+2) * ny * nx float64 values each, host or device memory (caller-owned; pinned
+ * host memory lets the copies overlap the steps).  Host inputs and outputs move through two
+ * device staging buffers per direction (4 (D+2) ny nx doubles, allocated on the first call and
+ * kept by the handle) on two copy streams of their own, so that run k+1's upload and run k-1's
+ * readback overlap run k's steps.  An output array must not overlap the input array of a later
+ * run.  steps_done (may be NULL) receives n_runs step counts.  On return no copy is in flight
+ * and the handle holds the last run's state (vlbm_step continues it).  Errors: VLBM_E_INVAL for
+ * n_runs, n_steps < 0, a null array or element, or a non-finite t_end (nothing runs);
+ * VLBM_E_STATE as vlbm_init; a failing run (VLBM_E_NONPHYSICAL, ...) ends the batch with its
+ * status: later runs do not start and their outputs are not written.  Synchronises. */
+vlbm_status vlbm_run_batch(vlbm_t h, int64_t n_runs, const double* const* W0s, int64_t n_steps, double t_end,
+                           double* const* Ws, int64_t* steps_done);
+
 /* beta(x) that the next step would use on the current state (Secs. III D; constant in
  * VLBM_BETA_CONST mode), ny * nx float64 values. */
 vlbm_status vlbm_get_beta(vlbm_t h, double* beta);

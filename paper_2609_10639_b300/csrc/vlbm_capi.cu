@@ -83,6 +83,12 @@ struct vlbm_s {
     Scalars* sc_backup = nullptr;
     double fwd_ms = 0.0, rev_ms = 0.0, recompute_ms = 0.0;
   } adj;
+  // vlbm_run_batch: device staging of host inputs and outputs ([4][nc * plane]: in 0, in 1,
+  // out 0, out 1; allocated on first use), one stream per copy direction, and the events that
+  // order the copies against the handle's stream: in_ready[2], in_free[2], out_ready[2], out_free[2]
+  double* bstage = nullptr;
+  cudaStream_t h2d = nullptr, d2h = nullptr;
+  cudaEvent_t bev[8] = {};
   bool profile = false;            // bracket step-kernel launches with events
   std::vector<cudaEvent_t> pev;    // event pool, used in pairs
   size_t pev_used = 0;
@@ -509,6 +515,8 @@ vlbm_status vlbm_create(const vlbm_grid* grid, const vlbm_eos* eos, const vlbm_p
 vlbm_status vlbm_destroy(vlbm_t h) {
   if (!h) return VLBM_OK;
   if (h->stream || h->cap_stream) cudaStreamSynchronize(h->stream);
+  if (h->h2d) cudaStreamSynchronize(h->h2d);
+  if (h->d2h) cudaStreamSynchronize(h->d2h);
   destroy_graphs(h);
   cudaFree(h->buf[0]);
   cudaFree(h->buf[1]);
@@ -545,6 +553,11 @@ vlbm_status vlbm_destroy(vlbm_t h) {
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  for (cudaEvent_t e : h->bev)
+    if (e) cudaEventDestroy(e);
+  if (h->h2d) cudaStreamDestroy(h->h2d);
+  if (h->d2h) cudaStreamDestroy(h->d2h);
+  cudaFree(h->bstage);
   delete h;
   return VLBM_OK;
 }
@@ -591,6 +604,27 @@ vlbm_status vlbm_set_inflow(vlbm_t h, const double* W_in) {
   return VLBM_OK;
 }
 
+namespace {
+
+// Equilibrium populations of W0 (device memory) on the handle's stream; resets time and counters.
+vlbm_status init_from_device(vlbm_t h, const double* src) {
+  vlbm::Launch L = launch_of(h, h->stream);
+  VLBM_TRY(vlbm::launch_init(L, h->precision, src, h->buf[0], h->partial, h->nblk_sum));
+  h->initialised = true;
+  h->unpulled = true;
+  h->last_step_pulled = false;
+  h->n_host = 0;
+  return VLBM_OK;
+}
+
+// W of the current state into device memory, on the handle's stream.
+cudaError_t get_W_to_device(vlbm_t h, double* dst) {
+  vlbm::Launch L = launch_of(h, h->stream);
+  return vlbm::launch_get_W(L, h->precision, h->buf[(int)(h->n_host & 1)], h->unpulled ? 0 : 1, dst);
+}
+
+}  // namespace
+
 vlbm_status vlbm_init(vlbm_t h, const double* W0) {
   if (!h || !W0) return VLBM_E_INVAL;
   if (h->p.bc[0] == VLBM_BC_INFLOW && !h->inflow_set) return VLBM_E_STATE;
@@ -600,13 +634,7 @@ vlbm_status vlbm_init(vlbm_t h, const double* W0) {
     VLBM_TRY(cudaMemcpyAsync(h->scratch, W0, wbytes, cudaMemcpyDefault, h->stream));
     src = h->scratch;
   }
-  vlbm::Launch L = launch_of(h, h->stream);
-  VLBM_TRY(vlbm::launch_init(L, h->precision, src, h->buf[0], h->partial, h->nblk_sum));
-  h->initialised = true;
-  h->unpulled = true;
-  h->last_step_pulled = false;
-  h->n_host = 0;
-  return VLBM_OK;
+  return init_from_device(h, src);
 }
 
 vlbm_status vlbm_step(vlbm_t h, int64_t n_steps, double t_end, int64_t* steps_done) {
@@ -657,16 +685,100 @@ vlbm_status vlbm_step(vlbm_t h, int64_t n_steps, double t_end, int64_t* steps_do
 vlbm_status vlbm_get_W(vlbm_t h, double* W) {
   if (!h || !W) return VLBM_E_INVAL;
   if (!h->initialised) return VLBM_E_STATE;
-  const int cur = (int)(h->n_host & 1);
   const bool dev = is_device_ptr(W);
-  double* dst = dev ? W : h->scratch;
-  vlbm::Launch L = launch_of(h, h->stream);
-  VLBM_TRY(vlbm::launch_get_W(L, h->precision, h->buf[cur], h->unpulled ? 0 : 1, dst));
+  VLBM_TRY(get_W_to_device(h, dev ? W : h->scratch));
   if (!dev) {
     VLBM_TRY(cudaMemcpyAsync(W, h->scratch, (size_t)h->p.nc * h->p.plane * sizeof(double), cudaMemcpyDefault, h->stream));
     VLBM_TRY(cudaStreamSynchronize(h->stream));
   }
   return VLBM_OK;
+}
+
+namespace {
+
+vlbm_status batch_resources(vlbm_t h) {
+  if (h->bstage) return VLBM_OK;
+  if (cudaStreamCreateWithFlags(&h->h2d, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&h->d2h, cudaStreamNonBlocking) != cudaSuccess)
+    return VLBM_E_CUDA;
+  for (cudaEvent_t& e : h->bev)
+    if (!e) VLBM_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  VLBM_TRY(cudaMalloc(&h->bstage, (size_t)4 * h->p.nc * h->p.plane * sizeof(double)));
+  return VLBM_OK;
+}
+
+}  // namespace
+
+vlbm_status vlbm_run_batch(vlbm_t h, int64_t n_runs, const double* const* W0s, int64_t n_steps, double t_end,
+                           double* const* Ws, int64_t* steps_done) {
+  if (!h || n_runs < 0 || n_steps < 0 || !std::isfinite(t_end)) return VLBM_E_INVAL;
+  if (n_runs == 0) return VLBM_OK;
+  if (!W0s || !Ws) return VLBM_E_INVAL;
+  for (int64_t k = 0; k < n_runs; ++k) {
+    if (!W0s[k] || !Ws[k]) return VLBM_E_INVAL;
+    if (steps_done) steps_done[k] = 0;
+  }
+  if (h->p.bc[0] == VLBM_BC_INFLOW && !h->inflow_set) return VLBM_E_STATE;
+  vlbm_status st = batch_resources(h);
+  if (st != VLBM_OK) {
+    cudaGetLastError();
+    return st;
+  }
+  const size_t n = (size_t)h->p.nc * h->p.plane, wbytes = n * sizeof(double);
+  double* const in[2] = {h->bstage, h->bstage + n};
+  double* const out[2] = {h->bstage + 2 * n, h->bstage + 3 * n};
+  cudaEvent_t* const in_ready = h->bev;
+  cudaEvent_t* const in_free = h->bev + 2;
+  cudaEvent_t* const out_ready = h->bev + 4;
+  cudaEvent_t* const out_free = h->bev + 6;
+  // Upload of run k into staging buffer k mod 2 on the upload stream, once the run two before
+  // it has read that buffer (vlbm_init of run k - 2).
+  auto upload = [&](int64_t k) -> cudaError_t {
+    if (is_device_ptr(W0s[k])) return cudaSuccess;
+    const int j = (int)(k & 1);
+    cudaError_t e = cudaStreamWaitEvent(h->h2d, in_free[j], 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(in[j], W0s[k], wbytes, cudaMemcpyHostToDevice, h->h2d);
+    if (e == cudaSuccess) e = cudaEventRecord(in_ready[j], h->h2d);
+    return e;
+  };
+  cudaError_t e = upload(0);
+  for (int64_t k = 0; k < n_runs && e == cudaSuccess && st == VLBM_OK; ++k) {
+    const int j = (int)(k & 1);
+    const bool dev_in = is_device_ptr(W0s[k]), dev_out = is_device_ptr(Ws[k]);
+    if (!dev_in) e = cudaStreamWaitEvent(h->stream, in_ready[j], 0);
+    if (e != cudaSuccess) break;
+    st = init_from_device(h, dev_in ? W0s[k] : in[j]);
+    if (st != VLBM_OK) break;
+    e = cudaEventRecord(in_free[j], h->stream);
+    // the next run's upload runs while this run steps
+    if (e == cudaSuccess && k + 1 < n_runs) e = upload(k + 1);
+    if (e != cudaSuccess) break;
+    int64_t done = 0;
+    st = vlbm_step(h, n_steps, t_end, &done);
+    if (steps_done) steps_done[k] = done;
+    if (st != VLBM_OK) break;
+    // W into staging buffer k mod 2 once the readback of run k - 2 has left it; its readback
+    // runs on the download stream while the next run steps
+    if (dev_out) {
+      e = get_W_to_device(h, Ws[k]);
+    } else {
+      e = cudaStreamWaitEvent(h->stream, out_free[j], 0);
+      if (e == cudaSuccess) e = get_W_to_device(h, out[j]);
+      if (e == cudaSuccess) e = cudaEventRecord(out_ready[j], h->stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(h->d2h, out_ready[j], 0);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(Ws[k], out[j], wbytes, cudaMemcpyDeviceToHost, h->d2h);
+      if (e == cudaSuccess) e = cudaEventRecord(out_free[j], h->d2h);
+    }
+  }
+  // no copy into or out of the caller's arrays is left in flight on return
+  const cudaError_t e1 = cudaStreamSynchronize(h->h2d);
+  const cudaError_t e2 = cudaStreamSynchronize(h->d2h);
+  const cudaError_t e3 = cudaStreamSynchronize(h->stream);
+  if (st != VLBM_OK) return st;
+  if (e != cudaSuccess) return cuda_status(e);
+  if (e1 != cudaSuccess) return cuda_status(e1);
+  if (e2 != cudaSuccess) return cuda_status(e2);
+  return cuda_status(e3);
 }
 
 vlbm_status vlbm_get_populations(vlbm_t h, double* f) {

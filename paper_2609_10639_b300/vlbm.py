@@ -77,6 +77,7 @@ def _load():
         "vlbm_load_state": [V, V, C.c_size_t],
         "vlbm_measure_fp64_peak": [I32, D],
         "vlbm_set_inflow": [V, V],
+        "vlbm_run_batch": [V, I64, C.POINTER(V), I64, C.c_double, C.POINTER(V), C.POINTER(I64)],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -119,6 +120,14 @@ def _ptr(a) -> int:
         return a.ctypes.data
     assert a.dtype.itemsize == 8 and a.is_contiguous(), "contiguous float64 tensor required"
     return a.data_ptr()
+
+
+def _ptr_n(a, n: int) -> int:
+    """_ptr of an array that must hold exactly n values (the library writes or reads all of them)."""
+    size = a.size if isinstance(a, np.ndarray) else a.numel()
+    if size != n:
+        raise ValueError(f"array of {size} values where {n} are required")
+    return _ptr(a)
 
 
 @dataclass
@@ -201,7 +210,7 @@ class Solver:
     def init(self, W0) -> None:
         if isinstance(W0, np.ndarray):
             W0 = np.ascontiguousarray(W0, dtype=np.float64).reshape(self.shape)
-        _check(_lib.vlbm_init(self._h, C.c_void_p(_ptr(W0))), "vlbm_init")
+        _check(_lib.vlbm_init(self._h, C.c_void_p(_ptr_n(W0, self.nc * self.ny * self.nx))), "vlbm_init")
         self._keep = W0  # the copy is stream-ordered; keep the source alive until it ran
 
     def step(self, n_steps: int, t_end: float = 0.0) -> int:
@@ -212,8 +221,25 @@ class Solver:
     def W(self, out=None):
         if out is None:
             out = self.torch.empty(self.shape, dtype=self.torch.float64, device=self.device)
-        _check(_lib.vlbm_get_W(self._h, C.c_void_p(_ptr(out))), "vlbm_get_W")
+        _check(_lib.vlbm_get_W(self._h, C.c_void_p(_ptr_n(out, self.nc * self.ny * self.nx))), "vlbm_get_W")
         return out
+
+    def run_batch(self, W0s, n_steps: int, t_end: float = 0.0, outs=None):
+        """Independent runs init(W0s[k]) + step(n_steps, t_end) + W(outs[k]), host copies of one
+        run overlapping the steps of the next (vlbm_run_batch).  Returns (outs, steps done)."""
+        n = len(W0s)
+        W0s = [np.ascontiguousarray(w, dtype=np.float64).reshape(self.shape) if isinstance(w, np.ndarray) else w
+               for w in W0s]
+        if outs is None:
+            outs = [self.torch.empty(self.shape, dtype=self.torch.float64, device=self.device) for _ in range(n)]
+        if len(outs) != n:
+            raise ValueError("one output per input")
+        m = self.nc * self.ny * self.nx
+        ins = (C.c_void_p * n)(*[_ptr_n(w, m) for w in W0s])
+        outp = (C.c_void_p * n)(*[_ptr_n(o, m) for o in outs])
+        done = (C.c_int64 * n)()
+        _check(_lib.vlbm_run_batch(self._h, n, ins, int(n_steps), float(t_end), outp, done), "vlbm_run_batch")
+        return outs, list(done)
 
     def beta(self) -> np.ndarray:
         out = np.empty((self.ny, self.nx))

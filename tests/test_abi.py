@@ -57,6 +57,7 @@ def test_create_rejects_bad_arguments_without_touching_the_gpu():
     e.gamma = 1.0
     assert L.vlbm_create(C.byref(g), C.byref(e), C.byref(p), None, C.byref(h)) == vlbm.E_INVAL
     assert L.vlbm_step(None, 1, 0.0, None) == vlbm.E_INVAL
+    assert L.vlbm_run_batch(None, 1, None, 1, 0.0, None, None) == vlbm.E_INVAL
     assert L.vlbm_destroy(None) == vlbm.OK
 
 
