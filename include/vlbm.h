@@ -238,15 +238,32 @@ vlbm_status vlbm_get_profile(vlbm_t h, double* ms_total, int64_t* launches);
  *   dJ_deos: host[5] output dJ/d(gamma, a, b, R, cv) (the ideal gas uses gamma, van der Waals
  *            a, b, R, cv), or NULL.
  * Not available on a grid with a pinned-inflow side or with VLBM_EOS_VDW_CVT (VLBM_E_UNSUPPORTED).
- * Afterwards the handle holds the final state of the run (as after vlbm_step).  Device memory:
- * (ceil(n_steps / checkpoint_every) + min(checkpoint_every, n_steps) + 2) population states plus
- * 43 FP64 fields per cell.  Synchronises. */
+ * Afterwards the handle holds the final state of the run (as after vlbm_step), and vlbm_step
+ * continues it.  Device memory: (ceil(n_steps / checkpoint_every) + min(checkpoint_every,
+ * n_steps) + 2) population states plus 43 FP64 fields per cell, plus the tape (see
+ * vlbm_set_adjoint_tape): the last segments of the run, as many as the tape limit allows, are
+ * stepped by the forward pass into slots of their own (each state, and on FP64 column strips the
+ * W, u, Q and sensor quantities of each state, 22 FP64 values per cell), so the reverse pass
+ * applies their adjoint steps without recomputing them.  The gradient is the same either way up
+ * to rounding (on FP64 strips the last state of a taped segment reads its kept quantities where a
+ * recomputed segment's adjoint evaluates them itself: 6e-15 relative measured).  The handle keeps
+ * the workspace and the tape for later calls.  Synchronises. */
 vlbm_status vlbm_adjoint(vlbm_t h, const double* W0, int64_t n_steps, int32_t checkpoint_every, const double* dJ_dWT,
                          double* dJ_dW0, double* dJ_deos);
 
 /* Device time (ms) of the reverse pass (segment recomputation and adjoint steps) of the last
  * vlbm_adjoint call, and of its segment recomputations alone (*recompute_ms, may be NULL). */
 vlbm_status vlbm_adjoint_timing(vlbm_t h, double* reverse_ms, double* recompute_ms);
+
+/* Limit of the adjoint tape, in bytes: max_bytes < 0 (the default) lets each vlbm_adjoint call
+ * use up to 3/4 of the device memory free at that moment; 0 disables the tape (every segment is
+ * recomputed from its checkpoint) and releases its memory; a positive value caps it (a held tape
+ * above the cap is released).  Synchronises when it releases memory. */
+vlbm_status vlbm_set_adjoint_tape(vlbm_t h, int64_t max_bytes);
+
+/* Of the last vlbm_adjoint call: device time (ms) of its forward pass, the steps whose states
+ * came from the tape rather than a recomputation, and the tape bytes used (each may be NULL). */
+vlbm_status vlbm_adjoint_info(vlbm_t h, double* forward_ms, int64_t* taped_steps, int64_t* tape_bytes);
 
 /* Number of kernel launches one time step issues (for launch accounting). */
 vlbm_status vlbm_launches_per_step(vlbm_t h, int32_t* launches);

@@ -60,7 +60,7 @@ struct vlbm_s {
   int gev_pending = -1;       // event set of the last profiled chunk launch, not yet read
   double prof_ms = 0.0;       // summed step-kernel time of the profiled chunks read so far
   long long prof_n = 0;       // their step-kernel launches
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
   // adjoint workspace (allocated on first use, grown when needed)
   struct Adj {
     double* ckpt = nullptr;   // checkpoint states
@@ -82,6 +82,13 @@ struct vlbm_s {
     vlbm::AdjScalars* as_host = nullptr;
     Scalars* sc_backup = nullptr;
     double fwd_ms = 0.0, rev_ms = 0.0, recompute_ms = 0.0;
+    // tape: the last segments' states (and, FP64 strips, their W, u, Q and sensor quantities)
+    // kept by the forward pass, so that the reverse pass does not recompute those segments
+    double* tape = nullptr;
+    size_t tape_cap = 0;          // doubles
+    long long tape_limit = -1;    // bytes; < 0: 3/4 of the free device memory; 0: no tape
+    long long taped_steps = 0;    // of the last call
+    size_t tape_used = 0;         // bytes of the last call
   } adj;
   // vlbm_run_batch: device staging of host inputs and outputs ([4][nc * plane]: in 0, in 1,
   // out 0, out 1; allocated on first use), one stream per copy direction, and the events that
@@ -478,7 +485,8 @@ vlbm_status vlbm_create(const vlbm_grid* grid, const vlbm_eos* eos, const vlbm_p
   h->scratch_elems = (size_t)p.nc * p.plane + p.plane + 8;
   h->nblk_sum = vlbm::sum_blocks(p);
   if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) {
+      cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess ||
+      cudaEventCreate(&h->ev2) != cudaSuccess) {
     st = VLBM_E_CUDA;
   } else if (cudaMalloc(&h->buf[0], fbytes) != cudaSuccess || cudaMalloc(&h->buf[1], fbytes) != cudaSuccess ||
              cudaMalloc(&h->sc, sizeof(Scalars)) != cudaSuccess ||
@@ -543,6 +551,7 @@ vlbm_status vlbm_destroy(vlbm_t h) {
   cudaFree(h->adj.sched);
   cudaFree(h->adj.dJ);
   cudaFree(h->adj.dW0);
+  cudaFree(h->adj.tape);
   cudaFree(h->adj.as);
   cudaFree(h->adj.sc_backup);
   if (h->adj.as_host) cudaFreeHost(h->adj.as_host);
@@ -552,6 +561,7 @@ vlbm_status vlbm_destroy(vlbm_t h) {
       if (e) cudaEventDestroy(e);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
+  if (h->ev2) cudaEventDestroy(h->ev2);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   for (cudaEvent_t e : h->bev)
     if (e) cudaEventDestroy(e);
@@ -1086,8 +1096,69 @@ vlbm_status vlbm_adjoint(vlbm_t h, const double* W0, int64_t n_steps, int32_t ch
         cudaMalloc(&A.as, sizeof(vlbm::AdjScalars)) != cudaSuccess)
       return VLBM_E_NOMEM;
   }
+  // Tape: the last T segments are stepped by the forward pass into slots of their own (every
+  // state of the segment, and for FP64 strips the W, u, Q and sensor quantities of each state,
+  // which the maxima pass and the step kernel write there), so the reverse pass applies their
+  // adjoint steps without recomputing them.  T is as large as the tape limit allows: by default
+  // 3/4 of the free device memory (a B300's HBM holds several hundred steps of a 1024^2 run).
+  const bool tape_kept = h->fields && p.dim == 2;
+  const size_t tape_seg = segn * state + (tape_kept ? segn * kept_per_state : 0);  // doubles
+  size_t T = 0;
+  if (A.tape_limit != 0) {
+    size_t budget = 0;
+    if (A.tape_limit > 0) {
+      budget = (size_t)A.tape_limit;
+    } else {
+      size_t fr = 0, tot = 0;
+      if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) budget = fr / 4 * 3 + A.tape_cap * sizeof(double);
+      cudaGetLastError();
+    }
+    T = budget / (tape_seg * sizeof(double));
+    if (T > nseg) T = nseg;
+    if (T > 0 && !grow(&A.tape, &A.tape_cap, T * tape_seg)) {
+      cudaGetLastError();
+      T = 0;
+    }
+  }
+  const size_t first_taped = nseg - T;
+  A.taped_steps = T > 0 ? N - (long long)first_taped * K : 0;
+  A.tape_used = T * tape_seg * sizeof(double);
   VLBM_TRY(cudaMemcpyAsync(A.dW0, W0, wsz * sizeof(double), cudaMemcpyDefault, h->stream));
   VLBM_TRY(cudaMemcpyAsync(A.dJ, dJ_dWT, wsz * sizeof(double), cudaMemcpyDefault, h->stream));
+
+  // One taped segment of the forward pass: from the handle's current state n0 (buffer n0 & 1),
+  // `steps` steps in the two-pass form with live link-speed decisions, as vlbm_step takes them,
+  // every state into the segment's slots and the last one into buffer (n0 + steps) & 1.
+  auto tape_forward = [&](size_t sgi, long long steps) -> vlbm_status {
+    const long long n0 = (long long)sgi * K;
+    if (h->n_host != n0) return VLBM_E_STATE;
+    vlbm_status ts = ensure_history(h, n0 + steps + 1);
+    if (ts != VLBM_OK) return ts;
+    double* tst = A.tape + (sgi - first_taped) * tape_seg;
+    double* tkp = tape_kept ? tst + segn * state : nullptr;
+    vlbm::Launch TL = launch_of(h, h->stream);
+    VLBM_TRY(vlbm::launch_begin(TL, 0.0));
+    VLBM_TRY(cudaMemcpyAsync(tst, h->buf[(int)(n0 & 1)], state * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    for (long long j = 0; j < steps; ++j) {
+      const long long n = n0 + j;
+      const int pulled = n >= 1 ? 1 : 0;  // the run's first step reads the equilibrium in place
+      double* fin = tst + (size_t)j * state;
+      void* fout = j + 1 < steps ? static_cast<void*>(tst + (size_t)(j + 1) * state) : h->buf[(int)((n + 1) & 1)];
+      if (tkp) {
+        TL.fields = tkp + (size_t)j * kept_per_state;
+        TL.sens = kept_sensor ? TL.fields + (size_t)14 * p.plane : nullptr;
+      }
+      VLBM_TRY(vlbm::launch_reduce(TL, h->precision, fin, pulled, true));
+      VLBM_TRY(vlbm::launch_dt(TL));
+      VLBM_TRY(vlbm::launch_step(TL, h->precision, false, fin, fout, pulled));
+    }
+    ts = sync_scalars(h);
+    if (ts != VLBM_OK) return ts;
+    if (h->n_host != n0 + steps) return VLBM_E_STATE;
+    h->unpulled = false;
+    h->last_step_pulled = true;
+    return VLBM_OK;
+  };
 
   // ---- forward pass: checkpoints every K steps, recorded link speeds ----
   VLBM_TRY(cudaEventRecord(h->ev0, h->stream));
@@ -1100,9 +1171,14 @@ vlbm_status vlbm_adjoint(vlbm_t h, const double* W0, int64_t n_steps, int32_t ch
                            reinterpret_cast<const char*>(h->sc) + offsetof(Scalars, wref), 4 * sizeof(double),
                            cudaMemcpyDeviceToDevice, h->stream));
   for (size_t sgi = 0; sgi < nseg; ++sgi) {
+    const long long steps = (long long)((N - (long long)sgi * K) < K ? (N - (long long)sgi * K) : K);
+    if (sgi >= first_taped) {
+      st = tape_forward(sgi, steps);
+      if (st != VLBM_OK) return st;
+      continue;
+    }
     const int cur = (int)(h->n_host & 1);
     VLBM_TRY(cudaMemcpyAsync(A.ckpt + sgi * state, h->buf[cur], state * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
-    const long long steps = (long long)((N - (long long)sgi * K) < K ? (N - (long long)sgi * K) : K);
     int64_t done = 0;
     st = vlbm_step(h, steps, 0.0, &done);
     if (st != VLBM_OK) return st;
@@ -1122,6 +1198,18 @@ vlbm_status vlbm_adjoint(vlbm_t h, const double* W0, int64_t n_steps, int32_t ch
   const size_t pev_base = h->pev_used;  // event pairs bracketing the recomputations
   for (long long sgi = (long long)nseg - 1; sgi >= 0; --sgi) {
     const long long n0 = sgi * K, n1 = (n0 + K < N) ? n0 + K : N;
+    if ((size_t)sgi >= first_taped) {  // taped: every state and its kept quantities are at hand
+      double* tst = A.tape + ((size_t)sgi - first_taped) * tape_seg;
+      double* tkp = tape_kept ? tst + segn * state : nullptr;
+      for (long long n = n1 - 1; n >= n0; --n) {
+        const int pulled = n >= 1 ? 1 : 0;
+        double* kept = tkp ? tkp + (size_t)(n - n0) * kept_per_state : nullptr;
+        VLBM_TRY(vlbm::adj_step(L, h->precision, tst + (size_t)(n - n0) * state, pulled, A.lam[li], A.lam[li ^ 1], n,
+                                kept, kept_sensor));
+        li ^= 1;
+      }
+      continue;
+    }
     VLBM_TRY(cudaMemcpyAsync(A.seg, A.ckpt + (size_t)sgi * state, state * sizeof(double), cudaMemcpyDeviceToDevice,
                              h->stream));
     if (n1 - n0 > 1) {  // recompute the segment's states with the recorded link speeds (two-pass form)
@@ -1153,14 +1241,24 @@ vlbm_status vlbm_adjoint(vlbm_t h, const double* W0, int64_t n_steps, int32_t ch
   }
   VLBM_TRY(vlbm::adj_init(L, A.dW0, A.lam[li], c0, A.dW0));
   VLBM_TRY(cudaMemcpyAsync(h->sc, A.sc_backup, sizeof(Scalars), cudaMemcpyDeviceToDevice, h->stream));
-  VLBM_TRY(cudaEventRecord(h->ev0, h->stream));
+  {
+    // the recomputations overwrote the partial maxima (and the kept pressure) that a look-ahead
+    // step reads for the state it starts from: take them again from the final state
+    vlbm::Launch RL = launch_of(h, h->stream);
+    const int cur = (int)(N & 1);
+    VLBM_TRY(vlbm::launch_reduce(RL, h->precision, h->buf[cur], 1, false));
+    VLBM_TRY(vlbm::launch_fill_pressure(RL, h->buf[cur], 1));
+  }
+  VLBM_TRY(cudaEventRecord(h->ev2, h->stream));
   VLBM_TRY(cudaMemcpyAsync(dJ_dW0, A.dW0, wsz * sizeof(double), cudaMemcpyDefault, h->stream));
   VLBM_TRY(cudaMemcpyAsync(A.as_host, A.as, sizeof(vlbm::AdjScalars), cudaMemcpyDeviceToHost, h->stream));
   VLBM_TRY(cudaStreamSynchronize(h->stream));
-  float r_ms = 0.f;
-  // ev0 was re-recorded at the end of the reverse pass: reverse = [ev1, ev0]
-  VLBM_TRY(cudaEventElapsedTime(&r_ms, h->ev1, h->ev0));
+  float r_ms = 0.f, f_ms = 0.f;
+  // forward pass = [ev0, ev1], reverse pass = [ev1, ev2]
+  VLBM_TRY(cudaEventElapsedTime(&r_ms, h->ev1, h->ev2));
+  VLBM_TRY(cudaEventElapsedTime(&f_ms, h->ev0, h->ev1));
   A.rev_ms = r_ms;
+  A.fwd_ms = f_ms;
   A.recompute_ms = 0.0;
   for (size_t e = pev_base; e + 1 < h->pev_used; e += 2) {
     float m = 0.f;
@@ -1172,6 +1270,26 @@ vlbm_status vlbm_adjoint(vlbm_t h, const double* W0, int64_t n_steps, int32_t ch
     for (int j = 0; j < 5; ++j) dJ_deos[j] = A.as_host->eos[j];
   st = sync_scalars(h);
   return st;
+}
+
+vlbm_status vlbm_set_adjoint_tape(vlbm_t h, int64_t max_bytes) {
+  if (!h) return VLBM_E_INVAL;
+  h->adj.tape_limit = max_bytes;
+  if (max_bytes == 0 || (max_bytes > 0 && h->adj.tape_cap * sizeof(double) > (size_t)max_bytes)) {
+    VLBM_TRY(cudaStreamSynchronize(h->stream));
+    cudaFree(h->adj.tape);
+    h->adj.tape = nullptr;
+    h->adj.tape_cap = 0;
+  }
+  return VLBM_OK;
+}
+
+vlbm_status vlbm_adjoint_info(vlbm_t h, double* forward_ms, int64_t* taped_steps, int64_t* tape_bytes) {
+  if (!h) return VLBM_E_INVAL;
+  if (forward_ms) *forward_ms = h->adj.fwd_ms;
+  if (taped_steps) *taped_steps = h->adj.taped_steps;
+  if (tape_bytes) *tape_bytes = (int64_t)h->adj.tape_used;
+  return VLBM_OK;
 }
 
 vlbm_status vlbm_adjoint_timing(vlbm_t h, double* reverse_ms, double* recompute_ms) {

@@ -78,6 +78,8 @@ def _load():
         "vlbm_measure_fp64_peak": [I32, D],
         "vlbm_set_inflow": [V, V],
         "vlbm_run_batch": [V, I64, C.POINTER(V), I64, C.c_double, C.POINTER(V), C.POINTER(I64)],
+        "vlbm_set_adjoint_tape": [V, I64],
+        "vlbm_adjoint_info": [V, D, C.POINTER(I64), C.POINTER(I64)],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -291,6 +293,16 @@ class Solver:
         ms, rc = C.c_double(), C.c_double()
         _check(_lib.vlbm_adjoint_timing(self._h, C.byref(ms), C.byref(rc)), "vlbm_adjoint_timing")
         return ms.value, rc.value
+
+    def set_adjoint_tape(self, max_bytes: int) -> None:
+        """Adjoint tape limit in bytes (< 0: 3/4 of the free device memory; 0: off)."""
+        _check(_lib.vlbm_set_adjoint_tape(self._h, int(max_bytes)), "vlbm_set_adjoint_tape")
+
+    def adjoint_info(self):
+        """(forward-pass ms, taped steps, tape bytes) of the last adjoint call."""
+        ms, n, b = C.c_double(), C.c_int64(), C.c_int64()
+        _check(_lib.vlbm_adjoint_info(self._h, C.byref(ms), C.byref(n), C.byref(b)), "vlbm_adjoint_info")
+        return ms.value, n.value, b.value
 
     def set_profiling(self, on: bool) -> None:
         _check(_lib.vlbm_set_profiling(self._h, 1 if on else 0), "vlbm_set_profiling")

@@ -63,8 +63,9 @@ def _dual_dJ(prob, W0, n, g, sched, v=None, deos=None, **over):
     return float(np.sum(g * dW[0]))
 
 
+@pytest.mark.parametrize("tape", ["tape", "recompute"])
 @pytest.mark.parametrize("case", list(_cases()))
-def test_adjoint_matches_dual_numbers(case):
+def test_adjoint_matches_dual_numbers(case, tape):
     import torch
 
     from oracle import oracle as O
@@ -75,7 +76,9 @@ def test_adjoint_matches_dual_numbers(case):
     dJ_dWT = np.zeros_like(W0)
     dJ_dWT[0] = g
     s = vlbm.Solver.for_problem(prob, **over)
+    s.set_adjoint_tape(-1 if tape == "tape" else 0)
     dW0, deos = s.adjoint(torch.from_numpy(W0).cuda(), n, K, torch.from_numpy(dJ_dWT).cuda())
+    assert s.adjoint_info()[1] == (n if tape == "tape" else 0)
     dW0 = dW0.cpu().numpy()
     assert s.time()[1] == n
     # the oracle's own link-speed sequence of the same run
@@ -220,3 +223,62 @@ def test_adjoint_vortex_128_twenty_directions():
         assert abs(got - ref) <= 1e-9 * abs(ref), (got, ref)
     ref = _dual_dJ(prob, W0, n, g, sched, deos={"gamma": 1.0})
     assert abs(deos[0] - ref) <= 1e-9 * abs(ref), (deos[0], ref)
+
+
+def _tape_segment_bytes(s, prob, K, n, precision):
+    """Bytes of one taped segment: its states in storage precision, and on FP64 column strips the
+    22 kept FP64 values per cell and state."""
+    plane = prob.nx * (prob.ny if prob.dim == 2 else 1)
+    state_vals = 2 * prob.dim * 4 * plane
+    state = state_vals if precision == "fp64" else (state_vals + 1) // 2
+    segn = min(K, n)
+    kept = 22 * plane if (precision == "fp64" and prob.dim == 2 and s.cfg.tiling != "tile") else 0
+    return 8 * segn * (state + kept)
+
+
+@pytest.mark.parametrize("precision,tiling", [("fp64", "strip"), ("fp64", "tile"), ("fp32_store", "strip")])
+def test_adjoint_tape_gives_the_recomputed_gradient(precision, tiling):
+    # the same run with the tape off, partly on (the last two segments taped) and on for the whole
+    # run: the same gradient (the taped states and kept quantities are those the recomputation
+    # produces), the reported taped steps and tape size, and a state that vlbm_step continues
+    # exactly as a plain run of the same steps
+    import torch
+
+    from paper_2609_10639_b300 import vlbm
+
+    prob = dataclasses.replace(wl.VORTEX_ADJOINT_2D.resized(96, 80), extent=(0.0, 10.0, 0.0, 10.0 * 80 / 96))
+    W0 = torch.from_numpy(wl.vortex_density_2d(prob)).cuda()
+    dJ = torch.zeros_like(W0)
+    dJ[0] = torch.from_numpy(_weight(prob)).cuda()
+    n, K = 45, 8  # six segments, the last one of five steps
+    out = {}
+    for mode in ("off", "two", "all"):
+        s = vlbm.Solver.for_problem(prob, precision=precision, tiling=tiling)
+        seg = _tape_segment_bytes(s, prob, K, n, precision)
+        s.set_adjoint_tape({"off": 0, "two": int(2.5 * seg), "all": -1}[mode])
+        dW0, deos = s.adjoint(W0, n, K, dJ)
+        fwd_ms, taped, used = s.adjoint_info()
+        assert taped == {"off": 0, "two": 8 + 5, "all": n}[mode], (mode, taped)
+        assert used == {"off": 0, "two": 2 * seg, "all": 6 * seg}[mode], (mode, used, seg)
+        assert fwd_ms > 0.0
+        assert s.time()[1] == n
+        s.step(7)  # continues the run's final state
+        out[mode] = (dW0.cpu().numpy(), deos, s.W().cpu().numpy())
+    plain = vlbm.Solver.for_problem(prob, precision=precision, tiling=tiling)
+    plain.init(W0)
+    plain.step(n + 7)
+    Wp = plain.W().cpu().numpy()
+    ref = out["off"]
+    for mode in ("two", "all"):
+        g, e, Wc = out[mode]
+        err = float(np.abs(g - ref[0]).max() / np.abs(ref[0]).max())
+        print(f"{precision}/{tiling}/{mode}: gradient rel max difference to the recomputation {err:.2e}")
+        assert err <= 1e-13, (mode, err)
+        np.testing.assert_allclose(e, ref[1], rtol=1e-13)
+    for mode in ("off", "two", "all"):
+        d = float(np.abs(out[mode][2] - Wp).max() / np.abs(Wp).max())
+        print(f"{precision}/{tiling}/{mode}: state 7 steps after the adjoint against a plain run: {d:.2e}")
+        # FP64 and the untaped FP32 run: the same kernels and decisions.  Taped FP32 segments are
+        # stepped in the two-pass form, the plain FP32 run in the look-ahead form (equal up to the
+        # rounding of the FP32 moments)
+        assert d <= (0.0 if precision == "fp64" or mode == "off" else 1e-6), (mode, d)
