@@ -198,8 +198,9 @@ def aggregate_mlups(world, cells, steps, ms):
     return world * cells * steps / (ms * 1e-3) / 1e6
 
 
-def time_path(prob, W0, precision, S, K, W, world, clocks_idx=None):
-    """Times K vlbm_step(S) calls on device-resident inputs after W untimed ones."""
+def time_path(prob, W0, precision, S, K, W, world, clocks_idx=None, profile=True):
+    """Times K vlbm_step(S) calls on device-resident inputs after W untimed ones (with profile, the
+    graph chunks carry event-record nodes around every step kernel, read for its mean time)."""
     import torch
 
     from paper_2609_10639_b300 import vlbm
@@ -208,7 +209,7 @@ def time_path(prob, W0, precision, S, K, W, world, clocks_idx=None):
     s.init(W0)
     for _ in range(W):
         s.step(S)
-    s.set_profiling(True)
+    s.set_profiling(profile)
     barrier(world)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -336,9 +337,13 @@ def other_workloads(S, K, W, world):
         W0 = torch.from_numpy(make(prob)).cuda()
         entry = {"grid": [prob.nx, prob.ny]}
         for prec in ("fp64", "fp32_store"):
-            r = time_path(prob, W0, prec, S, K, W, world)
+            # the production graphs for the throughput; a second, profiled run for the step
+            # kernel's time (the event-record nodes cost a few us per step, which small grids feel)
+            r = time_path(prob, W0, prec, S, K, W, world, profile=False)
+            rp = time_path(prob, W0, prec, S, K, W, world)
             entry[prec] = {"value": aggregate_mlups(world, prob.ncells, S * K, r["ms"]), "unit": UNIT,
-                           "ms_per_step": r["ms"] / K, "dominant_kernel_ms": r["kernel_ms_avg"]}
+                           "ms_per_step": r["ms"] / K, "dominant_kernel_ms": rp["kernel_ms_avg"],
+                           "value_profiled_run": aggregate_mlups(world, prob.ncells, S * K, rp["ms"])}
         out[prob.name] = entry
     return out
 

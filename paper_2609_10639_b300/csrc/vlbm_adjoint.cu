@@ -33,6 +33,11 @@ namespace vlbm {
 
 namespace {
 constexpr int kNTA = 256;
+// The per-CTA partials of a cell-parallel kernel are folded in two fixed-order stages: one warp
+// per group of kGroup partials, then one CTA of kNTF threads over the groups.  A single CTA over
+// all partials was bound by its one SM's FP64 pipe (2 FP64 results per clock per SM).
+constexpr int kGroup = 32;
+constexpr int kNTF = 128;
 
 // workspace field indices (each a plane of FP64 values)
 enum {
@@ -194,18 +199,47 @@ __device__ __forceinline__ bool better(double v, long long i, double bv, long lo
   return a > b || (a == b && i < bi);
 }
 
-// Smem tree reduction of per-thread (value, index) candidates over the CTA (kNTA threads) into
-// thread 0's slots.
-__device__ __forceinline__ void argmax_block(double (&sv)[kNTA][4], long long (&si)[kNTA][4], int nc) {
+constexpr long long kNoIndex = 0x7fffffffffffffffll;  // loses every comparison of better()
+
+// Warp-wide argmax of (value, index) pairs under better(), a strict total order on the pairs, so
+// the unique best pair results whatever the order of the comparisons.
+__device__ __forceinline__ void argmax_warp(double& v, long long& i) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const double ov = __shfl_xor_sync(0xffffffffu, v, off);
+    const long long oi = __shfl_xor_sync(0xffffffffu, i, off);
+    if (better(ov, oi, v, i)) {
+      v = ov;
+      i = oi;
+    }
+  }
+}
+
+// CTA-wide argmax of the per-thread candidates (v[k], i[k]), k < nc: within each warp by
+// shuffles, then over the warps' results by warp 0, whose lane 0 ends with the CTA's best pairs.
+template <int NT>
+__device__ __forceinline__ void argmax_cta(double (&v)[4], long long (&i)[4], int nc) {
+  __shared__ double wv[NT / 32][4];
+  __shared__ long long wi[NT / 32][4];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (k >= nc) break;
+    argmax_warp(v[k], i[k]);
+    if (lane == 0) {
+      wv[warp][k] = v[k];
+      wi[warp][k] = i[k];
+    }
+  }
   __syncthreads();
-  for (int s = kNTA / 2; s > 0; s >>= 1) {
-    if ((int)threadIdx.x < s)
-      for (int k = 0; k < nc; ++k)
-        if (better(sv[threadIdx.x + s][k], si[threadIdx.x + s][k], sv[threadIdx.x][k], si[threadIdx.x][k])) {
-          sv[threadIdx.x][k] = sv[threadIdx.x + s][k];
-          si[threadIdx.x][k] = si[threadIdx.x + s][k];
-        }
-    __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (k >= nc) break;
+      v[k] = lane < NT / 32 ? wv[lane][k] : 0.0;
+      i[k] = lane < NT / 32 ? wi[lane][k] : kNoIndex;
+      argmax_warp(v[k], i[k]);
+    }
   }
 }
 
@@ -215,14 +249,14 @@ __global__ void __launch_bounds__(kNTA) k_adj_fields(const S* __restrict__ fin, 
                                                       const AdjScalars* __restrict__ as, double* __restrict__ F,
                                                       double* __restrict__ pv, long long* __restrict__ pi) {
   constexpr int NC = D + 2;
-  __shared__ double sv[kNTA][4];
-  __shared__ long long si[kNTA][4];
+  double sv[4];
+  long long si[4];
   const int cell = blockIdx.x * kNTA + threadIdx.x;
   const long long P = p.plane;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    sv[threadIdx.x][k] = 0.0;
-    si[threadIdx.x][k] = 0x7fffffffffffffffll;
+    sv[k] = 0.0;
+    si[k] = kNoIndex;
   }
   if (cell < p.plane) {
     const int cx = cell % p.nx, cy = cell / p.nx;
@@ -252,14 +286,17 @@ __global__ void __launch_bounds__(kNTA) k_adj_fields(const S* __restrict__ fin, 
           ba = a;
         }
       }
-      sv[threadIdx.x][k] = __longlong_as_double((long long)best);
-      si[threadIdx.x][k] = (long long)(ba * NC + k) * P + cell;
+      sv[k] = __longlong_as_double((long long)best);
+      si[k] = (long long)(ba * NC + k) * P + cell;
     }
   }
-  argmax_block(sv, si, NC);
-  if ((int)threadIdx.x < NC) {
-    pv[blockIdx.x * 4 + threadIdx.x] = sv[0][threadIdx.x];
-    pi[blockIdx.x * 4 + threadIdx.x] = si[0][threadIdx.x];
+  argmax_cta<kNTA>(sv, si, NC);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      pv[blockIdx.x * 4 + k] = sv[k];
+      pi[blockIdx.x * 4 + k] = si[k];
+    }
   }
 }
 
@@ -269,14 +306,14 @@ template <int D>
 __global__ void __launch_bounds__(kNTA) k_adj_argmax_kept(const double* __restrict__ WQ, const KParams p,
                                                            double* __restrict__ pv, long long* __restrict__ pi) {
   constexpr int NC = D + 2;
-  __shared__ double sv[kNTA][4];
-  __shared__ long long si[kNTA][4];
+  double sv[4];
+  long long si[4];
   const int cell = blockIdx.x * kNTA + threadIdx.x;
   const long long P = p.plane;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    sv[threadIdx.x][k] = 0.0;
-    si[threadIdx.x][k] = 0x7fffffffffffffffll;
+    sv[k] = 0.0;
+    si[k] = kNoIndex;
   }
   if (cell < p.plane) {
 #pragma unroll
@@ -292,42 +329,78 @@ __global__ void __launch_bounds__(kNTA) k_adj_argmax_kept(const double* __restri
           ba = a;
         }
       }
-      sv[threadIdx.x][k] = __longlong_as_double((long long)best);
-      si[threadIdx.x][k] = (long long)(ba * NC + k) * P + cell;
+      sv[k] = __longlong_as_double((long long)best);
+      si[k] = (long long)(ba * NC + k) * P + cell;
     }
   }
-  argmax_block(sv, si, NC);
-  if ((int)threadIdx.x < NC) {
-    pv[blockIdx.x * 4 + threadIdx.x] = sv[0][threadIdx.x];
-    pi[blockIdx.x * 4 + threadIdx.x] = si[0][threadIdx.x];
+  argmax_cta<kNTA>(sv, si, NC);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      pv[blockIdx.x * 4 + k] = sv[k];
+      pi[blockIdx.x * 4 + k] = si[k];
+    }
   }
 }
 
 // Fold of the per-CTA candidates (one CTA): M_k, 1/M_k and the argmax of each k.
-__global__ void __launch_bounds__(kNTA) k_adj_argmax_fold(const double* __restrict__ pv, const long long* __restrict__ pi,
-                                                           int nparts, int nc, long long plane, AdjScalars* as) {
-  __shared__ double sv[kNTA][4];
-  __shared__ long long si[kNTA][4];
+// First stage: the best candidate of each group of kGroup per-CTA candidates (one warp each).
+__global__ void __launch_bounds__(kGroup) k_adj_argmax_groups(const double* __restrict__ pv,
+                                                              const long long* __restrict__ pi, int nparts, int nc,
+                                                              double* __restrict__ gv, long long* __restrict__ gi) {
+  const int c = blockIdx.x * kGroup + threadIdx.x;
+#pragma unroll
   for (int k = 0; k < 4; ++k) {
-    sv[threadIdx.x][k] = 0.0;
-    si[threadIdx.x][k] = 0x7fffffffffffffffll;
+    if (k >= nc) break;
+    double v = c < nparts ? pv[c * 4 + k] : 0.0;
+    long long i = c < nparts ? pi[c * 4 + k] : kNoIndex;
+    argmax_warp(v, i);
+    if (threadIdx.x == 0) {
+      gv[blockIdx.x * 4 + k] = v;
+      gi[blockIdx.x * 4 + k] = i;
+    }
   }
-  for (int c = threadIdx.x; c < nparts; c += kNTA)
-    for (int k = 0; k < nc; ++k)
-      if (better(pv[c * 4 + k], pi[c * 4 + k], sv[threadIdx.x][k], si[threadIdx.x][k])) {
-        sv[threadIdx.x][k] = pv[c * 4 + k];
-        si[threadIdx.x][k] = pi[c * 4 + k];
+}
+
+// Second stage over the groups' candidates.  Also sets the step's r = c_n / c_{n+1} and
+// 1/c_{n+1} from the recorded link speeds (read by k_adj_local, which runs after this fold).
+__global__ void __launch_bounds__(kNTF) k_adj_argmax_fold(const double* __restrict__ pv, const long long* __restrict__ pi,
+                                                           int nparts, int nc, long long plane, AdjScalars* as,
+                                                           const double* __restrict__ sched, long long n) {
+  double sv[4];
+  long long si[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    sv[k] = 0.0;
+    si[k] = kNoIndex;
+  }
+  for (int c = threadIdx.x; c < nparts; c += kNTF)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (k >= nc) break;
+      const double v = pv[c * 4 + k];
+      const long long i = pi[c * 4 + k];
+      if (better(v, i, sv[k], si[k])) {
+        sv[k] = v;
+        si[k] = i;
       }
-  argmax_block(sv, si, nc);
-  if ((int)threadIdx.x < nc) {
-    const int k = threadIdx.x;
-    const double bv = sv[0][k];
-    as->M[k] = bv;
-    as->invM[k] = bv > 0.0 ? 1.0 / bv : 0.0;
-    const long long idx = si[0][k];
-    as->amax[k] = idx;
-    as->amax_cell[k] = (int)(idx % plane);
-    as->amax_alpha[k] = (int)((idx / plane) / nc);
+    }
+  argmax_cta<kNTF>(sv, si, nc);
+  if (threadIdx.x == 0) {
+    const double c_old = sched[n], c_new = sched[n + 1];
+    as->r = c_old / c_new;
+    as->inv_c = 1.0 / c_new;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (k >= nc) break;
+      const double bv = sv[k];
+      as->M[k] = bv;
+      as->invM[k] = bv > 0.0 ? 1.0 / bv : 0.0;
+      const long long idx = si[k];
+      as->amax[k] = idx;
+      as->amax_cell[k] = (int)(idx % plane);
+      as->amax_alpha[k] = (int)((idx / plane) / nc);
+    }
   }
 }
 
@@ -611,22 +684,52 @@ __global__ void __launch_bounds__(kNTA) k_adj_filter(const KParams p, const AdjS
 }
 
 // Fixed-order (deterministic) fold of per-CTA partial sums: out[j] = sum_c part[c * 8 + j], j < nv.
-__global__ void __launch_bounds__(kNTA) k_adj_fold(const double* __restrict__ part, int nparts, int nv, double* out,
+// First stage: the sum of each group of kGroup per-CTA partials (one warp each, a fixed shuffle
+// tree).
+__global__ void __launch_bounds__(kGroup) k_adj_fold_groups(const double* __restrict__ part, int nparts, int nv,
+                                                            double* __restrict__ gpart) {
+  const int c = blockIdx.x * kGroup + threadIdx.x;
+#pragma unroll
+  for (int j = 0; j < 5; ++j) {
+    if (j >= nv) break;
+    double v = c < nparts ? part[c * 8 + j] : 0.0;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (threadIdx.x == 0) gpart[blockIdx.x * 8 + j] = v;
+  }
+}
+
+__global__ void __launch_bounds__(kNTF) k_adj_fold(const double* __restrict__ part, int nparts, int nv, double* out,
                                                     double* comp, int accumulate) {
-  __shared__ double red[kNTA][5];
+  // fixed order: thread t sums partials t, t + kNTF, ... in turn; then a fixed shuffle tree per
+  // warp and one over the warps (deterministic)
+  __shared__ double red[kNTF / 32][5];
   double v[5] = {0, 0, 0, 0, 0};
-  for (int c = threadIdx.x; c < nparts; c += kNTA)
-    for (int j = 0; j < nv; ++j) v[j] += part[c * 8 + j];
-  for (int j = 0; j < 5; ++j) red[threadIdx.x][j] = v[j];
+  for (int c = threadIdx.x; c < nparts; c += kNTF)
+#pragma unroll
+    for (int j = 0; j < 5; ++j)
+      if (j < nv) v[j] += part[c * 8 + j];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < 5; ++j) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v[j] += __shfl_xor_sync(0xffffffffu, v[j], off);
+    if (lane == 0) red[warp][j] = v[j];
+  }
   __syncthreads();
-  for (int s = kNTA / 2; s > 0; s >>= 1) {
-    if ((int)threadIdx.x < s)
-      for (int j = 0; j < 5; ++j) red[threadIdx.x][j] += red[threadIdx.x + s][j];
-    __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+      v[j] = lane < kNTF / 32 ? red[lane][j] : 0.0;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) v[j] += __shfl_xor_sync(0xffffffffu, v[j], off);
+    }
   }
   if (threadIdx.x == 0)
-    for (int j = 0; j < nv; ++j) {
-      const double x = red[0][j];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+      if (j >= nv) break;
+      const double x = v[j];
       if (!accumulate) {
         out[j] = x;
       } else {  // Neumaier-compensated running sum
@@ -795,12 +898,6 @@ __global__ void __launch_bounds__(kNTA) k_adj_init(const double* __restrict__ W0
   if ((int)threadIdx.x < 5) part[blockIdx.x * 8 + threadIdx.x] = red[0][threadIdx.x];
 }
 
-__global__ void k_adj_set_step(AdjScalars* as, const double* __restrict__ sched, long long n) {
-  const double c_old = sched[n], c_new = sched[n + 1];
-  as->r = c_old / c_new;
-  as->inv_c = 1.0 / c_new;
-}
-
 __global__ void k_adj_begin(AdjScalars* as) {
   for (int j = 0; j < 5; ++j) {
     as->eos[j] = 0.0;
@@ -833,23 +930,27 @@ double* adj_field(AdjScalars* as, size_t off) { return reinterpret_cast<double*>
 }  // namespace
 
 int adj_part_entries(const KParams& p) { return (int)cells_blocks(p) + 1; }
+int adj_group_entries(const KParams& p) { return (int)((cells_blocks(p) + kGroup - 1) / kGroup) + 1; }
 
 template <int D, class S>
 static cudaError_t adj_step_t(const AdjLaunch& A, const S* fin, int pulled, const double* lam_in, double* lam_out,
                               long long n, double* kept, bool kept_sensor) {
   const KParams& p = *A.p;
   const unsigned nb = cells_blocks(p);
-  k_adj_set_step<<<1, 1, 0, A.stream>>>(A.as, A.sched, n);
   double* WQ = kept ? kept : A.F;  // planes F_W .. F_VORT of this step
   if (kept) k_adj_argmax_kept<D><<<nb, kNTA, 0, A.stream>>>(kept, p, A.pv, A.pi);
   else k_adj_fields<D, S><<<nb, kNTA, 0, A.stream>>>(fin, p, pulled, A.as, A.F, A.pv, A.pi);
-  k_adj_argmax_fold<<<1, kNTA, 0, A.stream>>>(A.pv, A.pi, nb, p.nc, p.plane, A.as);
+  const unsigned ng = (nb + kGroup - 1) / kGroup;
+  k_adj_argmax_groups<<<ng, kGroup, 0, A.stream>>>(A.pv, A.pi, nb, p.nc, A.gpart, A.gidx);
+  k_adj_argmax_fold<<<1, kNTF, 0, A.stream>>>(A.gpart, A.gidx, ng, p.nc, p.plane, A.as, A.sched, n);
   if (!(kept && kept_sensor)) k_adj_sensor<D><<<nb, kNTA, 0, A.stream>>>(p, A.as, WQ, WQ);
   k_adj_local<D, S><<<nb, kNTA, 0, A.stream>>>(fin, lam_in, lam_out, p, pulled, A.as, A.F, WQ);
   k_adj_filter<D><<<nb, kNTA, 0, A.stream>>>(p, A.as, A.F, A.part, WQ);
-  k_adj_fold<<<1, kNTA, 0, A.stream>>>(A.part, nb, p.nc, adj_field(A.as, offsetof(AdjScalars, lamM)), nullptr, 0);
+  k_adj_fold_groups<<<ng, kGroup, 0, A.stream>>>(A.part, nb, p.nc, A.gpart);
+  k_adj_fold<<<1, kNTF, 0, A.stream>>>(A.gpart, ng, p.nc, adj_field(A.as, offsetof(AdjScalars, lamM)), nullptr, 0);
   k_adj_flux<D><<<nb, kNTA, 0, A.stream>>>(lam_out, p, A.as, A.F, A.part, WQ);
-  k_adj_fold<<<1, kNTA, 0, A.stream>>>(A.part, nb, 5, adj_field(A.as, offsetof(AdjScalars, eos)),
+  k_adj_fold_groups<<<ng, kGroup, 0, A.stream>>>(A.part, nb, 5, A.gpart);
+  k_adj_fold<<<1, kNTF, 0, A.stream>>>(A.gpart, ng, 5, adj_field(A.as, offsetof(AdjScalars, eos)),
                                        adj_field(A.as, offsetof(AdjScalars, eos_comp)), 1);
   return cudaGetLastError();
 }
@@ -877,7 +978,9 @@ cudaError_t adj_init(const AdjLaunch& A, const double* W0, const double* lam0, d
   const unsigned nb = cells_blocks(p);
   if (p.dim == 1) k_adj_init<1><<<nb, kNTA, 0, A.stream>>>(W0, lam0, p, c0, dJ_dW0, A.part);
   else k_adj_init<2><<<nb, kNTA, 0, A.stream>>>(W0, lam0, p, c0, dJ_dW0, A.part);
-  k_adj_fold<<<1, kNTA, 0, A.stream>>>(A.part, nb, 5, adj_field(A.as, offsetof(AdjScalars, eos)),
+  const unsigned ng = (nb + kGroup - 1) / kGroup;
+  k_adj_fold_groups<<<ng, kGroup, 0, A.stream>>>(A.part, nb, 5, A.gpart);
+  k_adj_fold<<<1, kNTF, 0, A.stream>>>(A.gpart, ng, 5, adj_field(A.as, offsetof(AdjScalars, eos)),
                                        adj_field(A.as, offsetof(AdjScalars, eos_comp)), 1);
   k_adj_finish<<<1, 1, 0, A.stream>>>(A.as);
   return cudaGetLastError();

@@ -27,10 +27,13 @@ struct AdjLaunch {
   double* pv;           // per-CTA argmax values [CTAs][4]
   long long* pi;        // per-CTA argmax indices [CTAs][4]
   double* part;         // per-CTA partial sums [adj_part_entries][8]
+  double* gpart;        // first fold stage: group sums [adj_group_entries][8], or argmax values [..][4]
+  long long* gidx;      // first fold stage: argmax indices [adj_group_entries][4]
 };
 
 int adj_num_fields();
 int adj_part_entries(const KParams& p);
+int adj_group_entries(const KParams& p);
 // lambda^n from lambda^{n+1} for forward step n whose state f^n is `fin` (pulled or in place),
 // stored in FP64 (precision 0) or as FP32 deviations (precision 1).  `kept`: 22 planes in the
 // layout of the workspace's first planes (W, u, Q, s_hat, s, theta, dil, vort) of f^n, the

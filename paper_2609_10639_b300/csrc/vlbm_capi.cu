@@ -74,6 +74,8 @@ struct vlbm_s {
     double* pv = nullptr;
     long long* pi = nullptr;
     double* part = nullptr;
+    double* gpart = nullptr;  // first stage of the folds of the per-CTA partials
+    long long* gidx = nullptr;
     double* sched = nullptr;  // [c0, c_0, ..., c_{N-1}]
     size_t sched_cap = 0;
     double* dJ = nullptr;     // device copy of dJ/dW(T)
@@ -548,6 +550,8 @@ vlbm_status vlbm_destroy(vlbm_t h) {
   cudaFree(h->adj.pv);
   cudaFree(h->adj.pi);
   cudaFree(h->adj.part);
+  cudaFree(h->adj.gpart);
+  cudaFree(h->adj.gidx);
   cudaFree(h->adj.sched);
   cudaFree(h->adj.dJ);
   cudaFree(h->adj.dW0);
@@ -1090,6 +1094,8 @@ vlbm_status vlbm_adjoint(vlbm_t h, const double* W0, int64_t n_steps, int32_t ch
         cudaMalloc(&A.pv, (size_t)vlbm::adj_part_entries(p) * 4 * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&A.pi, (size_t)vlbm::adj_part_entries(p) * 4 * sizeof(long long)) != cudaSuccess ||
         cudaMalloc(&A.part, (size_t)vlbm::adj_part_entries(p) * 8 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&A.gpart, (size_t)vlbm::adj_group_entries(p) * 8 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&A.gidx, (size_t)vlbm::adj_group_entries(p) * 4 * sizeof(long long)) != cudaSuccess ||
         cudaMalloc(&A.dJ, wsz * sizeof(double)) != cudaSuccess || cudaMalloc(&A.dW0, wsz * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&A.sc_backup, sizeof(Scalars)) != cudaSuccess ||
         cudaMallocHost(&A.as_host, sizeof(vlbm::AdjScalars)) != cudaSuccess ||
@@ -1190,7 +1196,7 @@ vlbm_status vlbm_adjoint(vlbm_t h, const double* W0, int64_t n_steps, int32_t ch
   VLBM_TRY(cudaEventRecord(h->ev1, h->stream));
 
   // ---- reverse pass ----
-  vlbm::AdjLaunch L{&p, A.as, h->stream, A.sched, A.F, A.pv, A.pi, A.part};
+  vlbm::AdjLaunch L{&p, A.as, h->stream, A.sched, A.F, A.pv, A.pi, A.part, A.gpart, A.gidx};
   vlbm::Launch FL = launch_of(h, h->stream);
   FL.sched = A.sched;
   int li = (int)(N & 1);  // lambda^N lives in lam[li]
