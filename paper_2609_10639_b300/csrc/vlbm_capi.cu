@@ -623,7 +623,7 @@ namespace {
 // Equilibrium populations of W0 (device memory) on the handle's stream; resets time and counters.
 vlbm_status init_from_device(vlbm_t h, const double* src) {
   vlbm::Launch L = launch_of(h, h->stream);
-  VLBM_TRY(vlbm::launch_init(L, h->precision, src, h->buf[0], h->partial, h->nblk_sum));
+  VLBM_TRY(vlbm::launch_init(L, h->precision, src, h->buf[0], h->partial, h->nblk_sum, h->lookahead || h->pkeep));
   h->initialised = true;
   h->unpulled = true;
   h->last_step_pulled = false;

@@ -112,7 +112,9 @@ cudaError_t launch_reduce(const Launch& L, int precision, const void* fin, int p
 cudaError_t launch_dt(const Launch& L);
 cudaError_t launch_step(const Launch& L, int precision, bool lookahead, const void* fin, void* fout, int pulled);
 cudaError_t launch_beta(const Launch& L, int precision, const void* fin, int pulled, double* beta_out);
-cudaError_t launch_init(const Launch& L, int precision, const double* W0, void* fout, double* partial, int nblk_sum);
+// maxima: also the maxima of the stored initial populations (the look-ahead form's first step)
+cudaError_t launch_init(const Launch& L, int precision, const double* W0, void* fout, double* partial, int nblk_sum,
+                        bool maxima);
 cudaError_t launch_get_W(const Launch& L, int precision, const void* fin, int pulled, double* W);
 cudaError_t launch_get_f(const Launch& L, int precision, const void* fin, int pulled, double* f);
 cudaError_t launch_begin(const Launch& L, double t_end);

@@ -530,7 +530,9 @@ __global__ void __launch_bounds__(kNTD) k_init_c0(Scalars* sc, const KParams p, 
 
 // f_i = f_i^eq(W0; c0) (Eq. 20), stored in place (unpulled); maxima of W^0 = sum_i f_i into
 // partial slot 0.
-template <int D, class S, int NT>
+// MAXIMA: also the maxima of the stored populations into partial slot 0, which the first step of
+// the look-ahead form reads (the two-pass form's first step takes them itself).
+template <int D, class S, int NT, bool MAXIMA>
 __global__ void __launch_bounds__(NT) k_init_eq(const double* __restrict__ W0, S* __restrict__ fout, Scalars* __restrict__ sc,
                                                  const KParams p, double* __restrict__ part, float* __restrict__ pk) {
   using M = typename Store<S>::M;
@@ -543,7 +545,7 @@ __global__ void __launch_bounds__(NT) k_init_eq(const double* __restrict__ W0, S
 #pragma unroll
   for (int k = 0; k < NC; ++k) wq[k] = Store<S>::kOffset ? (M)(Q * sc->wref[k]) : (M)0;
   bool bad = false;
-  const double c0 = sc->c_prev;
+  const double h2c = 0.5 / sc->c_prev;  // 1 / (2 c0): c_i.Q / (2 c^2) with |c_i| = c
   static_assert(sizeof(S) == 4 || sizeof(S) == 8, "storage type");
   for (long long cell = (long long)blockIdx.x * NT + threadIdx.x; cell < p.plane; cell += (long long)gridDim.x * NT) {
     double W[NC], u[D], Qf[D][NC], cs;
@@ -557,20 +559,24 @@ __global__ void __launch_bounds__(NT) k_init_eq(const double* __restrict__ W0, S
       for (int i = 0; i < Q; ++i) {
         const int a = i >> 1;
         const double sgn = (i & 1) ? 1.0 : -1.0;
-        const double fe = W[k] / (2.0 * D) + sgn * Qf[a][k] / (2.0 * c0);  // c_i.Q/(2c^2), |c_i| = c
+        const double fe = W[k] * (1.0 / (2.0 * D)) + sgn * (Qf[a][k] * h2c);
         const S st = Store<S>::kOffset ? (S)(fe - sc->wref[k]) : (S)fe;
         fr[i][k] = (M)st;
       }
     store_cell<D, S, M>(fout, p, (int)cell, fr);
-    M Ws[NC], us[D], Qs[D][NC], css;
-    moments<D, M, Store<S>::kOffset>(fr, wq, Ws);
-    M Pc;
-    bad |= !prim_flux<D, M, true>(p, Ws, us, Qs, css, &Pc);
-    if (pk) pk[cell] = (float)Pc;  // kept pressure of the state n = 0 (slot 0)
-    cell_maxima<D, M>(us, css, Qs, v);
+    if constexpr (MAXIMA) {
+      M Ws[NC], us[D], Qs[D][NC], css;
+      moments<D, M, Store<S>::kOffset>(fr, wq, Ws);
+      M Pc;
+      bad |= !prim_flux<D, M, true>(p, Ws, us, Qs, css, &Pc);
+      if (pk) pk[cell] = (float)Pc;  // kept pressure of the state n = 0 (slot 0)
+      cell_maxima<D, M>(us, css, Qs, v);
+    }
   }
-  if (bad) atomicOr(&sc->err, ERR_NONPHYSICAL);
-  block_max_store<M, NT>(v, part, blockIdx.x, gridDim.x, &sc->nparts[0]);
+  if constexpr (MAXIMA) {
+    if (bad) atomicOr(&sc->err, ERR_NONPHYSICAL);
+    block_max_store<M, NT>(v, part, blockIdx.x, gridDim.x, &sc->nparts[0]);
+  }
 }
 
 // W = sum_i f_i (FP32 storage: FP64 sum of the reference share and the deviations).
@@ -799,7 +805,8 @@ cudaError_t launch_beta(const Launch& L, int precision, const void* fin, int pul
   return launch_tile_d<float, false, true>(L, fin, nullptr, pulled, invM_beta + 4, beta_out);
 }
 
-cudaError_t launch_init(const Launch& L, int precision, const double* W0, void* fout, double* partial, int nblk_sum) {
+cudaError_t launch_init(const Launch& L, int precision, const double* W0, void* fout, double* partial, int nblk_sum,
+                        bool maxima) {
   const KParams& p = *L.p;
   k_init_begin<<<1, 1, 0, L.stream>>>(L.sc);
   if (p.dim == 1) k_reduce_W0<1, kNT1><<<blocks_gs(p), kNT1, 0, L.stream>>>(W0, L.sc, p, L.part);
@@ -809,13 +816,18 @@ cudaError_t launch_init(const Launch& L, int precision, const double* W0, void* 
     k_sum_final<<<1, 1, 0, L.stream>>>(partial, nblk_sum, p, L.sc);
   }
   k_init_c0<<<1, kNTD, 0, L.stream>>>(L.sc, p, L.part, L.sched);
+  const unsigned g = blocks_gs(p);
+#define VLBM_INIT_EQ(D, S, PK)                                                                          \
+  (maxima ? k_init_eq<D, S, kNT1, true><<<g, kNT1, 0, L.stream>>>(W0, (S*)fout, L.sc, p, L.part, PK)    \
+          : k_init_eq<D, S, kNT1, false><<<g, kNT1, 0, L.stream>>>(W0, (S*)fout, L.sc, p, L.part, PK))
   if (p.dim == 1) {
-    if (precision == 0) k_init_eq<1, double, kNT1><<<blocks_gs(p), kNT1, 0, L.stream>>>(W0, (double*)fout, L.sc, p, L.part, nullptr);
-    else k_init_eq<1, float, kNT1><<<blocks_gs(p), kNT1, 0, L.stream>>>(W0, (float*)fout, L.sc, p, L.part, nullptr);
+    if (precision == 0) VLBM_INIT_EQ(1, double, nullptr);
+    else VLBM_INIT_EQ(1, float, nullptr);
   } else {
-    if (precision == 0) k_init_eq<2, double, kNT1><<<blocks_gs(p), kNT1, 0, L.stream>>>(W0, (double*)fout, L.sc, p, L.part, nullptr);
-    else k_init_eq<2, float, kNT1><<<blocks_gs(p), kNT1, 0, L.stream>>>(W0, (float*)fout, L.sc, p, L.part, L.pkeep);
+    if (precision == 0) VLBM_INIT_EQ(2, double, nullptr);
+    else VLBM_INIT_EQ(2, float, L.pkeep);
   }
+#undef VLBM_INIT_EQ
   return cudaGetLastError();
 }
 
