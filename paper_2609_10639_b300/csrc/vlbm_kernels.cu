@@ -471,47 +471,72 @@ __global__ void __launch_bounds__(NT) k_sum_partial(const double* __restrict__ W
     ss[threadIdx.x] = s;
     sc_[threadIdx.x] = c;
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
+      // fixed order: lane l folds the threads [l NT/32, (l+1) NT/32), then the lanes in order
+      constexpr int PER = NT / 32;
       double S = 0.0, Cc = 0.0;
-      for (int j = 0; j < NT; ++j) {
+      for (int j = threadIdx.x * PER; j < (threadIdx.x + 1) * PER; ++j) {
         const double x = ss[j];
         const double t = S + x;
         Cc += fabs(S) >= fabs(x) ? (S - t) + x : (x - t) + S;
         S = t;
         Cc += sc_[j];
       }
-      partial[blockIdx.x * 4 + k] = S + Cc;
+      double T = 0.0, Ct = 0.0;
+      for (int l = 0; l < 32; ++l) {
+        const double x = __shfl_sync(0xffffffffu, S, l), cx = __shfl_sync(0xffffffffu, Cc, l);
+        const double t = T + x;
+        Ct += fabs(T) >= fabs(x) ? (T - t) + x : (x - t) + T;
+        T = t;
+        Ct += cx;
+      }
+      if (threadIdx.x == 0) partial[blockIdx.x * 4 + k] = T + Ct;
     }
     __syncthreads();
   }
 }
 
+// Compensated (Neumaier) sum of the per-block partials of component k by one warp, in a fixed
+// order: lane l folds the contiguous blocks [l n/32, (l+1) n/32), then lane 0 folds the 32 lane
+// sums in lane order and adds their compensations.  Returns the total in lane 0.
+__device__ double warp_sum_partials(const double* __restrict__ partial, int nblk, int k) {
+  const int lane = threadIdx.x & 31;
+  const int b0 = (int)((long long)nblk * lane / 32), b1 = (int)((long long)nblk * (lane + 1) / 32);
+  double S = 0.0, Cc = 0.0;
+  for (int b = b0; b < b1; ++b) {
+    const double x = partial[b * 4 + k];
+    const double t = S + x;
+    Cc += fabs(S) >= fabs(x) ? (S - t) + x : (x - t) + S;
+    S = t;
+  }
+  double T = 0.0, Ct = 0.0;
+  for (int l = 0; l < 32; ++l) {
+    const double x = __shfl_sync(0xffffffffu, S, l), cx = __shfl_sync(0xffffffffu, Cc, l);
+    const double t = T + x;
+    Ct += fabs(T) >= fabs(x) ? (T - t) + x : (x - t) + T;
+    T = t;
+    Ct += cx;
+  }
+  return T + Ct;
+}
+
+// One warp.
 __global__ void k_sum_final(const double* __restrict__ partial, int nblk, const KParams p, Scalars* sc) {
   for (int k = 0; k < p.nc; ++k) {
-    double S = 0.0, Cc = 0.0;
-    for (int b = 0; b < nblk; ++b) {
-      const double x = partial[b * 4 + k];
-      const double t = S + x;
-      Cc += fabs(S) >= fabs(x) ? (S - t) + x : (x - t) + S;
-      S = t;
+    const double total = warp_sum_partials(partial, nblk, k);
+    if (threadIdx.x == 0) {
+      sc->wref[k] = total / (double)p.plane / (double)p.q;
+      sc->wq_f[k] = (float)(p.q * sc->wref[k]);
     }
-    sc->wref[k] = (S + Cc) / (double)p.plane / (double)p.q;
-    sc->wq_f[k] = (float)(p.q * sc->wref[k]);
   }
 }
 
-// Domain totals sum_x W_k of the current state: the per-block partials of k_sum_partial folded in
-// block order with the same compensation (the discrete conservation law of the step, Sec. III A).
+// Domain totals sum_x W_k of the current state: the per-block partials of k_sum_partial folded
+// with the same compensation (the discrete conservation law of the step, Sec. III A).  One warp.
 __global__ void k_sum_out(const double* __restrict__ partial, int nblk, const KParams p, double* __restrict__ out) {
   for (int k = 0; k < p.nc; ++k) {
-    double S = 0.0, Cc = 0.0;
-    for (int b = 0; b < nblk; ++b) {
-      const double x = partial[b * 4 + k];
-      const double t = S + x;
-      Cc += fabs(S) >= fabs(x) ? (S - t) + x : (x - t) + S;
-      S = t;
-    }
-    out[k] = S + Cc;
+    const double total = warp_sum_partials(partial, nblk, k);
+    if (threadIdx.x == 0) out[k] = total;
   }
 }
 
@@ -813,7 +838,7 @@ cudaError_t launch_init(const Launch& L, int precision, const double* W0, void* 
   else k_reduce_W0<2, kNT1><<<blocks_gs(p), kNT1, 0, L.stream>>>(W0, L.sc, p, L.part);
   if (precision == 1) {
     k_sum_partial<kNT1><<<nblk_sum, kNT1, 0, L.stream>>>(W0, p, partial);
-    k_sum_final<<<1, 1, 0, L.stream>>>(partial, nblk_sum, p, L.sc);
+    k_sum_final<<<1, 32, 0, L.stream>>>(partial, nblk_sum, p, L.sc);
   }
   k_init_c0<<<1, kNTD, 0, L.stream>>>(L.sc, p, L.part, L.sched);
   const unsigned g = blocks_gs(p);
@@ -861,7 +886,7 @@ cudaError_t launch_totals(const Launch& L, int precision, const void* fin, int p
   cudaError_t e = launch_get_W(L, precision, fin, pulled, W);
   if (e != cudaSuccess) return e;
   k_sum_partial<kNT1><<<nblk_sum, kNT1, 0, L.stream>>>(W, p, partial);
-  k_sum_out<<<1, 1, 0, L.stream>>>(partial, nblk_sum, p, out);
+  k_sum_out<<<1, 32, 0, L.stream>>>(partial, nblk_sum, p, out);
   return cudaGetLastError();
 }
 

@@ -58,6 +58,8 @@ def test_create_rejects_bad_arguments_without_touching_the_gpu():
     assert L.vlbm_create(C.byref(g), C.byref(e), C.byref(p), None, C.byref(h)) == vlbm.E_INVAL
     assert L.vlbm_step(None, 1, 0.0, None) == vlbm.E_INVAL
     assert L.vlbm_run_batch(None, 1, None, 1, 0.0, None, None) == vlbm.E_INVAL
+    assert L.vlbm_set_adjoint_tape(None, -1) == vlbm.E_INVAL
+    assert L.vlbm_adjoint_info(None, None, None, None) == vlbm.E_INVAL
     assert L.vlbm_destroy(None) == vlbm.OK
 
 

@@ -123,3 +123,25 @@ def test_batch_argument_checks():
     with pytest.raises(ValueError):
         g.run_batch([W0], 5, outs=[])
     assert g.run_batch([], 5) == ([], [])
+
+
+def test_batch_on_a_pinned_inflow_grid():
+    # the pinned-inflow boundary: the batch needs the inflow state as vlbm_init does, and each run
+    # equals its sequential counterpart
+    import torch
+
+    from paper_2609_10639_b300 import vlbm
+
+    prob = wl.SHOCK_VORTEX_IDEAL.resized(120, 45)
+    W0 = wl.shock_vortex_2d(prob)
+    runs = [W0, W0 * 1.05]
+    s = vlbm.Solver(vlbm.Config(dim=2, nx=prob.nx, ny=prob.ny, extent=prob.extent, bc=prob.bc, eos=prob.eos))
+    with pytest.raises(vlbm.VLBMError) as ei:
+        s.run_batch([torch.from_numpy(w).cuda() for w in runs], 10)
+    assert ei.value.status == vlbm.E_STATE
+    g = vlbm.Solver.for_problem(prob)
+    outs, done = g.run_batch([torch.from_numpy(w).pin_memory() for w in runs], 40)
+    assert done == [40, 40]
+    ref = sequential(prob, runs, 40)
+    for k in range(2):
+        np.testing.assert_array_equal(outs[k].cpu().numpy(), ref[k][0])
