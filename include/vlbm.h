@@ -242,12 +242,14 @@ vlbm_status vlbm_get_profile(vlbm_t h, double* ms_total, int64_t* launches);
  * continues it.  Device memory: (ceil(n_steps / checkpoint_every) + min(checkpoint_every,
  * n_steps) + 2) population states plus 43 FP64 fields per cell, plus the tape (see
  * vlbm_set_adjoint_tape): the last segments of the run, as many as the tape limit allows, are
- * stepped by the forward pass into slots of their own (each state, and on FP64 column strips the
- * W, u, Q and sensor quantities of each state, 22 FP64 values per cell), so the reverse pass
- * applies their adjoint steps without recomputing them.  The gradient is the same either way up
- * to rounding (on FP64 strips the last state of a taped segment reads its kept quantities where a
- * recomputed segment's adjoint evaluates them itself: 6e-15 relative measured).  The handle keeps
- * the workspace and the tape for later calls.  Synchronises. */
+ * stepped by the forward pass into slots of their own, so the reverse pass applies their adjoint
+ * steps without recomputing them.  A slot holds each state of its segment and, on FP64 column
+ * strips in sensor mode, the 8 sensor planes of each state (lean slot: the adjoint evaluates W, u,
+ * Q itself) or all 22 kept planes (full slot); the memory left after the lean slots makes the last
+ * ones full.  The gradient is the same either way up to rounding (6e-15 relative measured on FP64
+ * strips, where taped and recomputed segments take W, u, Q and the sensor quantities from
+ * different kernels).  The handle keeps the workspace and the tape for later calls.
+ * Synchronises. */
 vlbm_status vlbm_adjoint(vlbm_t h, const double* W0, int64_t n_steps, int32_t checkpoint_every, const double* dJ_dWT,
                          double* dJ_dW0, double* dJ_deos);
 

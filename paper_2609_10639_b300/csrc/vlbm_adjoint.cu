@@ -934,16 +934,21 @@ int adj_group_entries(const KParams& p) { return (int)((cells_blocks(p) + kGroup
 
 template <int D, class S>
 static cudaError_t adj_step_t(const AdjLaunch& A, const S* fin, int pulled, const double* lam_in, double* lam_out,
-                              long long n, double* kept, bool kept_sensor) {
+                              long long n, double* kept, bool kept_sensor, const double* sensor) {
   const KParams& p = *A.p;
   const unsigned nb = cells_blocks(p);
   double* WQ = kept ? kept : A.F;  // planes F_W .. F_VORT of this step
+  if (!kept && sensor) {
+    const cudaError_t e = cudaMemcpyAsync(A.F + (size_t)F_SH * p.plane, sensor, (size_t)8 * p.plane * sizeof(double),
+                                          cudaMemcpyDeviceToDevice, A.stream);
+    if (e != cudaSuccess) return e;
+  }
   if (kept) k_adj_argmax_kept<D><<<nb, kNTA, 0, A.stream>>>(kept, p, A.pv, A.pi);
   else k_adj_fields<D, S><<<nb, kNTA, 0, A.stream>>>(fin, p, pulled, A.as, A.F, A.pv, A.pi);
   const unsigned ng = (nb + kGroup - 1) / kGroup;
   k_adj_argmax_groups<<<ng, kGroup, 0, A.stream>>>(A.pv, A.pi, nb, p.nc, A.gpart, A.gidx);
   k_adj_argmax_fold<<<1, kNTF, 0, A.stream>>>(A.gpart, A.gidx, ng, p.nc, p.plane, A.as, A.sched, n);
-  if (!(kept && kept_sensor)) k_adj_sensor<D><<<nb, kNTA, 0, A.stream>>>(p, A.as, WQ, WQ);
+  if (!(kept && kept_sensor) && !(!kept && sensor)) k_adj_sensor<D><<<nb, kNTA, 0, A.stream>>>(p, A.as, WQ, WQ);
   k_adj_local<D, S><<<nb, kNTA, 0, A.stream>>>(fin, lam_in, lam_out, p, pulled, A.as, A.F, WQ);
   k_adj_filter<D><<<nb, kNTA, 0, A.stream>>>(p, A.as, A.F, A.part, WQ);
   k_adj_fold_groups<<<ng, kGroup, 0, A.stream>>>(A.part, nb, p.nc, A.gpart);
@@ -956,13 +961,13 @@ static cudaError_t adj_step_t(const AdjLaunch& A, const S* fin, int pulled, cons
 }
 
 cudaError_t adj_step(const AdjLaunch& A, int precision, const void* fin, int pulled, const double* lam_in, double* lam_out,
-                     long long n, double* kept, bool kept_sensor) {
-  if (A.p->dim == 1) kept = nullptr;  // kept fields exist for 2D strips only
+                     long long n, double* kept, bool kept_sensor, const double* sensor) {
+  if (A.p->dim == 1) kept = nullptr, sensor = nullptr;  // kept fields exist for 2D strips only
   if (precision == 0)
-    return A.p->dim == 1 ? adj_step_t<1, double>(A, (const double*)fin, pulled, lam_in, lam_out, n, kept, kept_sensor)
-                         : adj_step_t<2, double>(A, (const double*)fin, pulled, lam_in, lam_out, n, kept, kept_sensor);
-  return A.p->dim == 1 ? adj_step_t<1, float>(A, (const float*)fin, pulled, lam_in, lam_out, n, kept, kept_sensor)
-                       : adj_step_t<2, float>(A, (const float*)fin, pulled, lam_in, lam_out, n, kept, kept_sensor);
+    return A.p->dim == 1 ? adj_step_t<1, double>(A, (const double*)fin, pulled, lam_in, lam_out, n, kept, kept_sensor, sensor)
+                         : adj_step_t<2, double>(A, (const double*)fin, pulled, lam_in, lam_out, n, kept, kept_sensor, sensor);
+  return A.p->dim == 1 ? adj_step_t<1, float>(A, (const float*)fin, pulled, lam_in, lam_out, n, kept, kept_sensor, sensor)
+                       : adj_step_t<2, float>(A, (const float*)fin, pulled, lam_in, lam_out, n, kept, kept_sensor, sensor);
 }
 
 cudaError_t adj_terminal(const AdjLaunch& A, const double* dJ_dW, double* lam) {

@@ -38,9 +38,11 @@ int adj_group_entries(const KParams& p);
 // stored in FP64 (precision 0) or as FP32 deviations (precision 1).  `kept`: 22 planes in the
 // layout of the workspace's first planes (W, u, Q, s_hat, s, theta, dil, vort) of f^n, the
 // first 14 stored by the maxima pass of the forward recomputation and, with kept_sensor, the
-// other 8 by its step kernel; nullptr to recompute them all.
+// other 8 by its step kernel; nullptr to recompute them all.  `sensor` (with kept == nullptr): the
+// 8 sensor planes of f^n (s_hat, s, theta, dil, vort) written by the forward step kernel, so that
+// only W, u, Q are evaluated here; nullptr to evaluate them too.
 cudaError_t adj_step(const AdjLaunch& A, int precision, const void* fin, int pulled, const double* lam_in, double* lam_out,
-                     long long n, double* kept, bool kept_sensor);
+                     long long n, double* kept, bool kept_sensor, const double* sensor = nullptr);
 // lambda^N from dJ/dW(T); resets the EOS-gradient accumulator
 cudaError_t adj_terminal(const AdjLaunch& A, const double* dJ_dW, double* lam);
 // dJ/dW0 from lambda^0 through f^0 = f^eq(W0; c0); finishes the EOS-gradient sum

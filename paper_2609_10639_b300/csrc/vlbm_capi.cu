@@ -1102,14 +1102,20 @@ vlbm_status vlbm_adjoint(vlbm_t h, const double* W0, int64_t n_steps, int32_t ch
         cudaMalloc(&A.as, sizeof(vlbm::AdjScalars)) != cudaSuccess)
       return VLBM_E_NOMEM;
   }
-  // Tape: the last T segments are stepped by the forward pass into slots of their own (every
-  // state of the segment, and for FP64 strips the W, u, Q and sensor quantities of each state,
-  // which the maxima pass and the step kernel write there), so the reverse pass applies their
-  // adjoint steps without recomputing them.  T is as large as the tape limit allows: by default
-  // 3/4 of the free device memory (a B300's HBM holds several hundred steps of a 1024^2 run).
+  // Tape: the last T segments are stepped by the forward pass into slots of their own, so the
+  // reverse pass applies their adjoint steps without recomputing them.  A lean slot keeps every
+  // state of the segment and, on FP64 strips in sensor mode, the 8 sensor planes of each state
+  // (written by the step kernel), whose adjoint then evaluates W, u, Q itself; a full slot keeps
+  // all 22 planes (W, u, Q from the maxima pass too).  T is as large as the tape limit allows in
+  // lean slots (by default 3/4 of the free device memory: a B300's HBM holds about a thousand
+  // steps of a 1024^2 run that way); the memory left over turns the last T_full of them into
+  // full slots.  Avoiding a recomputation saves about a forward step per step, a full slot about
+  // a fifth of one more.
   const bool tape_kept = h->fields && p.dim == 2;
-  const size_t tape_seg = segn * state + (tape_kept ? segn * kept_per_state : 0);  // doubles
-  size_t T = 0;
+  const size_t sens_per_state = kept_sensor ? (size_t)8 * p.plane : 0;
+  const size_t lean_seg = segn * state + (tape_kept ? segn * sens_per_state : 0);      // doubles
+  const size_t full_seg = segn * state + (tape_kept ? segn * kept_per_state : 0);
+  size_t T = 0, T_full = 0;
   if (A.tape_limit != 0) {
     size_t budget = 0;
     if (A.tape_limit > 0) {
@@ -1119,16 +1125,37 @@ vlbm_status vlbm_adjoint(vlbm_t h, const double* W0, int64_t n_steps, int32_t ch
       if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) budget = fr / 4 * 3 + A.tape_cap * sizeof(double);
       cudaGetLastError();
     }
-    T = budget / (tape_seg * sizeof(double));
+    T = budget / (lean_seg * sizeof(double));
     if (T > nseg) T = nseg;
-    if (T > 0 && !grow(&A.tape, &A.tape_cap, T * tape_seg)) {
+    if (full_seg > lean_seg) {
+      T_full = (budget / sizeof(double) - T * lean_seg) / (full_seg - lean_seg);
+      if (T_full > T) T_full = T;
+    }
+    if (T > 0 && !grow(&A.tape, &A.tape_cap, (T - T_full) * lean_seg + T_full * full_seg)) {
       cudaGetLastError();
-      T = 0;
+      T = T_full = 0;
     }
   }
-  const size_t first_taped = nseg - T;
+  const size_t first_taped = nseg - T, first_full = nseg - T_full;
   A.taped_steps = T > 0 ? N - (long long)first_taped * K : 0;
-  A.tape_used = T * tape_seg * sizeof(double);
+  A.tape_used = ((T - T_full) * lean_seg + T_full * full_seg) * sizeof(double);
+  // a taped segment's slot: its states, then its kept planes (22 per state in a full slot, the
+  // 8 sensor planes in a lean one); lean slots first, the full ones (the last segments) after
+  struct TapeSlot {
+    double* states;
+    double* kept;     // full slot: 22 planes per state (nullptr otherwise)
+    double* sensor;   // lean slot in sensor mode: 8 planes per state (nullptr otherwise)
+  };
+  auto tape_slot = [&](size_t sgi) -> TapeSlot {
+    const bool full = sgi >= first_full;
+    double* base = A.tape + (full ? (first_full - first_taped) * lean_seg + (sgi - first_full) * full_seg
+                                  : (sgi - first_taped) * lean_seg);
+    double* extra = base + segn * state;
+    TapeSlot t{base, nullptr, nullptr};
+    if (tape_kept && full) t.kept = extra;
+    if (tape_kept && !full && kept_sensor) t.sensor = extra;
+    return t;
+  };
   VLBM_TRY(cudaMemcpyAsync(A.dW0, W0, wsz * sizeof(double), cudaMemcpyDefault, h->stream));
   VLBM_TRY(cudaMemcpyAsync(A.dJ, dJ_dWT, wsz * sizeof(double), cudaMemcpyDefault, h->stream));
 
@@ -1140,8 +1167,8 @@ vlbm_status vlbm_adjoint(vlbm_t h, const double* W0, int64_t n_steps, int32_t ch
     if (h->n_host != n0) return VLBM_E_STATE;
     vlbm_status ts = ensure_history(h, n0 + steps + 1);
     if (ts != VLBM_OK) return ts;
-    double* tst = A.tape + (sgi - first_taped) * tape_seg;
-    double* tkp = tape_kept ? tst + segn * state : nullptr;
+    const TapeSlot ts_ = tape_slot(sgi);
+    double* tst = ts_.states;
     vlbm::Launch TL = launch_of(h, h->stream);
     VLBM_TRY(vlbm::launch_begin(TL, 0.0));
     VLBM_TRY(cudaMemcpyAsync(tst, h->buf[(int)(n0 & 1)], state * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
@@ -1150,9 +1177,11 @@ vlbm_status vlbm_adjoint(vlbm_t h, const double* W0, int64_t n_steps, int32_t ch
       const int pulled = n >= 1 ? 1 : 0;  // the run's first step reads the equilibrium in place
       double* fin = tst + (size_t)j * state;
       void* fout = j + 1 < steps ? static_cast<void*>(tst + (size_t)(j + 1) * state) : h->buf[(int)((n + 1) & 1)];
-      if (tkp) {
-        TL.fields = tkp + (size_t)j * kept_per_state;
+      if (ts_.kept) {
+        TL.fields = ts_.kept + (size_t)j * kept_per_state;
         TL.sens = kept_sensor ? TL.fields + (size_t)14 * p.plane : nullptr;
+      } else if (ts_.sensor) {  // W, u, Q in the handle's own planes; the sensor planes taped
+        TL.sens = ts_.sensor + (size_t)j * sens_per_state;
       }
       VLBM_TRY(vlbm::launch_reduce(TL, h->precision, fin, pulled, true));
       VLBM_TRY(vlbm::launch_dt(TL));
@@ -1204,14 +1233,15 @@ vlbm_status vlbm_adjoint(vlbm_t h, const double* W0, int64_t n_steps, int32_t ch
   const size_t pev_base = h->pev_used;  // event pairs bracketing the recomputations
   for (long long sgi = (long long)nseg - 1; sgi >= 0; --sgi) {
     const long long n0 = sgi * K, n1 = (n0 + K < N) ? n0 + K : N;
-    if ((size_t)sgi >= first_taped) {  // taped: every state and its kept quantities are at hand
-      double* tst = A.tape + ((size_t)sgi - first_taped) * tape_seg;
-      double* tkp = tape_kept ? tst + segn * state : nullptr;
+    if ((size_t)sgi >= first_taped) {  // taped: every state (and its kept planes) at hand
+      const TapeSlot t = tape_slot((size_t)sgi);
       for (long long n = n1 - 1; n >= n0; --n) {
         const int pulled = n >= 1 ? 1 : 0;
-        double* kept = tkp ? tkp + (size_t)(n - n0) * kept_per_state : nullptr;
-        VLBM_TRY(vlbm::adj_step(L, h->precision, tst + (size_t)(n - n0) * state, pulled, A.lam[li], A.lam[li ^ 1], n,
-                                kept, kept_sensor));
+        const size_t j = (size_t)(n - n0);
+        double* kept = t.kept ? t.kept + j * kept_per_state : nullptr;
+        const double* sensor = t.sensor ? t.sensor + j * sens_per_state : nullptr;
+        VLBM_TRY(vlbm::adj_step(L, h->precision, t.states + j * state, pulled, A.lam[li], A.lam[li ^ 1], n, kept,
+                                kept_sensor, sensor));
         li ^= 1;
       }
       continue;

@@ -63,9 +63,11 @@ def _dual_dJ(prob, W0, n, g, sched, v=None, deos=None, **over):
     return float(np.sum(g * dW[0]))
 
 
-@pytest.mark.parametrize("tape", ["tape", "recompute"])
+@pytest.mark.parametrize("tape", ["tape", "lean_tape", "recompute"])
 @pytest.mark.parametrize("case", list(_cases()))
 def test_adjoint_matches_dual_numbers(case, tape):
+    # tape: every segment in a full slot; lean_tape: every segment in a lean slot (states and sensor
+    # planes; the adjoint evaluates W, u, Q itself); recompute: no tape
     import torch
 
     from oracle import oracle as O
@@ -76,9 +78,11 @@ def test_adjoint_matches_dual_numbers(case, tape):
     dJ_dWT = np.zeros_like(W0)
     dJ_dWT[0] = g
     s = vlbm.Solver.for_problem(prob, **over)
-    s.set_adjoint_tape(-1 if tape == "tape" else 0)
+    nseg = -(-n // K)
+    lean, _ = _tape_slot_doubles(s, prob, K, n, "fp64")
+    s.set_adjoint_tape({"tape": -1, "lean_tape": 8 * nseg * lean, "recompute": 0}[tape])
     dW0, deos = s.adjoint(torch.from_numpy(W0).cuda(), n, K, torch.from_numpy(dJ_dWT).cuda())
-    assert s.adjoint_info()[1] == (n if tape == "tape" else 0)
+    assert s.adjoint_info()[1] == (0 if tape == "recompute" else n)
     dW0 = dW0.cpu().numpy()
     assert s.time()[1] == n
     # the oracle's own link-speed sequence of the same run
@@ -225,23 +229,30 @@ def test_adjoint_vortex_128_twenty_directions():
     assert abs(deos[0] - ref) <= 1e-9 * abs(ref), (deos[0], ref)
 
 
-def _tape_segment_bytes(s, prob, K, n, precision):
-    """Bytes of one taped segment: its states in storage precision, and on FP64 column strips the
-    22 kept FP64 values per cell and state."""
+def _tape_slot_doubles(s, prob, K, n, precision):
+    """Doubles of one lean and one full tape slot: the segment's states in storage precision, plus
+    on FP64 column strips the 8 sensor planes (lean) or all 22 kept planes (full) per state."""
     plane = prob.nx * (prob.ny if prob.dim == 2 else 1)
     state_vals = 2 * prob.dim * 4 * plane
     state = state_vals if precision == "fp64" else (state_vals + 1) // 2
     segn = min(K, n)
-    kept = 22 * plane if (precision == "fp64" and prob.dim == 2 and s.cfg.tiling != "tile") else 0
-    return 8 * segn * (state + kept)
+    strips64 = precision == "fp64" and prob.dim == 2 and s.cfg.tiling != "tile"
+    return segn * (state + (8 * plane if strips64 else 0)), segn * (state + (22 * plane if strips64 else 0))
+
+
+def _expected_tape(cap_bytes, lean, full, nseg):
+    """As many lean slots as fit, the last of them made full with the memory left over."""
+    T = min(nseg, cap_bytes // (8 * lean))
+    Tf = min(T, (cap_bytes // 8 - T * lean) // (full - lean)) if full > lean else 0
+    return T, Tf
 
 
 @pytest.mark.parametrize("precision,tiling", [("fp64", "strip"), ("fp64", "tile"), ("fp32_store", "strip")])
 def test_adjoint_tape_gives_the_recomputed_gradient(precision, tiling):
-    # the same run with the tape off, partly on (the last two segments taped) and on for the whole
-    # run: the same gradient (the taped states and kept quantities are those the recomputation
-    # produces), the reported taped steps and tape size, and a state that vlbm_step continues
-    # exactly as a plain run of the same steps
+    # the same run with the tape off, partly on (a limit of 2.5 full slots: on FP64 strips three
+    # lean slots, the last made full) and on for the whole run: the same gradient (the taped
+    # states and kept quantities are those the recomputation produces), the reported taped steps
+    # and tape size, and a state that vlbm_step continues exactly as a plain run of the same steps
     import torch
 
     from paper_2609_10639_b300 import vlbm
@@ -251,15 +262,18 @@ def test_adjoint_tape_gives_the_recomputed_gradient(precision, tiling):
     dJ = torch.zeros_like(W0)
     dJ[0] = torch.from_numpy(_weight(prob)).cuda()
     n, K = 45, 8  # six segments, the last one of five steps
+    steps = [8, 8, 8, 8, 8, 5]
     out = {}
     for mode in ("off", "two", "all"):
         s = vlbm.Solver.for_problem(prob, precision=precision, tiling=tiling)
-        seg = _tape_segment_bytes(s, prob, K, n, precision)
-        s.set_adjoint_tape({"off": 0, "two": int(2.5 * seg), "all": -1}[mode])
+        lean, full = _tape_slot_doubles(s, prob, K, n, precision)
+        cap = {"off": 0, "two": int(2.5 * 8 * full), "all": -1}[mode]
+        s.set_adjoint_tape(cap)
         dW0, deos = s.adjoint(W0, n, K, dJ)
         fwd_ms, taped, used = s.adjoint_info()
-        assert taped == {"off": 0, "two": 8 + 5, "all": n}[mode], (mode, taped)
-        assert used == {"off": 0, "two": 2 * seg, "all": 6 * seg}[mode], (mode, used, seg)
+        T, Tf = {"off": (0, 0), "all": (6, 6)}.get(mode) or _expected_tape(cap, lean, full, 6)
+        assert taped == sum(steps[6 - T:]), (mode, taped, T)
+        assert used == 8 * ((T - Tf) * lean + Tf * full), (mode, used, T, Tf)
         assert fwd_ms > 0.0
         assert s.time()[1] == n
         s.step(7)  # continues the run's final state
