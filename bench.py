@@ -483,9 +483,9 @@ def run_ours(args):
                 "reverse_over_forward": adj["rev_ms"] / adj["fwd_ms"],
                 "adjoint_step_over_forward_step": (adj["rev_ms"] - adj["rec_ms"]) / adj["fwd_ms"],
                 "tape": {"taped_steps": adj["taped_steps"], "bytes": adj["tape_bytes"],
-                         "note": "the forward pass keeps the last segments' states and their W, u, Q and sensor "
-                                 "quantities in HBM (up to 3/4 of the free memory), so the reverse pass "
-                                 "recomputes only the other segments"},
+                         "note": "the forward pass keeps the last segments' states (with their sensor planes, "
+                                 "and W, u, Q where memory is left) in HBM, up to 3/4 of the free memory, so the "
+                                 "reverse pass recomputes only the other segments"},
                 "adjoint_forward_pass_ms": adj["adj_fwd_ms"],
                 "whole_call_over_forward": (adj["adj_fwd_ms"] + adj["rev_ms"]) / adj["fwd_ms"],
                 "without_tape": {"reverse_ms": adj["rev_ms_no_tape"], "recompute_ms": adj["rec_ms_no_tape"],
