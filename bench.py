@@ -499,7 +499,8 @@ def run_ours(args):
                              "kernels": "the adjoint-step kernels (k_adj_local, k_adj_flux, k_adj_filter and "
                                         "the folds) over the reverse pass minus its segment recomputation",
                              "note": "every adjoint kernel is FP64-pipe bound (ncu: "
-                                     "profiles/adjoint_kernels_vortex_1024.md)",
+                                     "profiles/adjoint_kernels_vortex_1024.md); a step taped in a lean slot "
+                                     "also evaluates W, u, Q (k_adj_fields, not counted in flops_per_cell)",
                              "hbm_achieved_gbs": ADJ_BYTES_PER_CELL * adj["cells"] * adj["steps"] / (adj["rev_ms"] * 1e-3) / 1e9,
                              "hbm_frac": ADJ_BYTES_PER_CELL * adj["cells"] * adj["steps"] / (adj["rev_ms"] * 1e-3) / 1e9 / pk["hbm_gbs"],
                              "hbm_bytes_per_cell": ADJ_BYTES_PER_CELL}},
