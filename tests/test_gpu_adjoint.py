@@ -153,6 +153,16 @@ def test_adjoint_vortex_1024_central_differences():
         assert abs(ad - fd) <= 1e-4 * abs(fd), (ad, fd)
     fdg = float((gd * (rho_T(W0d, 1.4 + eps) - rho_T(W0d, 1.4 - eps))).sum()) / (2 * eps)
     assert abs(deos[0] - fdg) <= 1e-4 * abs(fdg), (deos[0], fdg)
+    # the same gradient with every segment recomputed from its checkpoint (the tape, which held
+    # the whole run above, off)
+    assert s.adjoint_info()[1] == n
+    s.set_adjoint_tape(0)
+    dW0r, deosr = s.adjoint(W0d, n, K, dJ)
+    assert s.adjoint_info()[1] == 0
+    err = float((dW0r - dW0).abs().max() / dW0.abs().max())
+    print(f"1024^2 adjoint, recomputed segments against the tape: {err:.2e}")
+    assert err <= 1e-12
+    assert abs(deosr[0] - deos[0]) <= 1e-12 * abs(deos[0])
 
 
 def test_autograd_function_matches_adjoint():
