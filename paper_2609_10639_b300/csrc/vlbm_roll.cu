@@ -45,7 +45,7 @@ struct RollGeom {
   // Relaxed-population rings, one per direction, each as deep as the rows S4 still reads after
   // S3 wrote rows [F-RR, F): x pairs and f*_{y-} (read at the row itself, or the row below it
   // only where that is the edge row) [F-RR-1, F); f*_{y+} (read from the row above) [F-RR-2, F).
-  // The y- ring is one row short of the others: 4 resident CTAs per SM in FP32.
+  // The y- ring is one row short of the others (less shared memory per resident CTA).
   __host__ __device__ static constexpr int RF(int i) { return i == 2 ? RR + 1 : RR + 2; }
   __host__ __device__ static constexpr int OF(int i) { return i <= 2 ? i * (RR + 2) : 2 * (RR + 2) + RR + 1; }
   // FP64 two-pass form: the x pass of the box filter runs once per row in a stage of its own (S2x)
@@ -75,7 +75,7 @@ __device__ __forceinline__ int ring(int r, int base) {
   return (int)((unsigned)(r - base + 8 * R) % (unsigned)R);
 }
 
-// FP32 storage: 1024 resident threads per SM (64 registers) to hide memory latency (0.46 vs
+// FP32 storage: about 1024 resident threads per SM (64 registers) to hide memory latency (0.46 vs
 // 0.73 ms per two-pass step kernel at 4096^2 with half of them); FP64 is bound by its FP64 pipe
 // and runs two CTAs of up to 128 registers per SM, so that one CTA's stage S1 (loads only, with
 // W, u, Q kept by the maxima pass) overlaps the other's arithmetic.  INFLOW: the grid has a
@@ -437,13 +437,17 @@ __global__ void __launch_bounds__(XW * RR, sizeof(S) == 4 ? 1024 / (XW * RR) : 5
 }
 
 // Strip shapes: XW columns per row (TXO = XW - 2H of them outputs), RR rows per iteration.
-// FP32 storage: 128 x 2 threads (rings of 3-4 rows, 54 KB, four CTAs per SM); measured on a B300
-// at 4096^2 the two-pass step kernel takes 0.42 ms this way against 0.46 ms with 128 x 4.
+// FP32 storage: 160 x 2 threads (rings of 3-4 rows, 69 KB, three CTAs per SM); measured on a B300
+// at 4096^2 the look-ahead step kernel takes 0.459 ms this way against 0.480 ms with 128 x 2 (four
+// CTAs per SM), 0.479 with 96 x 2 (five) and 0.503-0.519 with 192, 224 or 256 x 2 (two); with
+// 128 x 4 the two-pass step kernel took 0.46 against 0.42 ms with 128 x 2.  KEEP (a non-ideal gas,
+// whose FP64 equation of state bounds the kernel) keeps 128 x 2 and four CTAs per SM: 7,417 against
+// 7,155 MLUPS on the 2048^2 van der Waals interface.
 // FP64: 128 x 2 threads, two CTAs per SM (4.90 ms per two-pass step kernel at 4096^2 against
 // 5.26 ms with one CTA of 128 x 4, whose FP64 pipe idled while all its warps were in S1).
-template <class S, bool LOOK>
+template <class S, bool LOOK, bool KEEP = false>
 struct RollCfg {
-  static constexpr int XW = 128, RR = 2;
+  static constexpr int XW = sizeof(S) == 4 && !KEEP ? 160 : 128, RR = 2;
 };
 
 constexpr int kMaxDevices = 64;
@@ -456,7 +460,7 @@ constexpr int cfg_index() {
 
 template <class S, bool LOOK, bool INFLOW, bool KEEP = false>
 cudaError_t launch_roll_t(const Launch& L_, const void* fin, void* fout, int pulled, const void* invM) {
-  using C = RollCfg<S, LOOK>;
+  using C = RollCfg<S, LOOK, KEEP>;
   using G = RollGeom<S, LOOK, C::XW, C::RR>;
   const KParams& p = *L_.p;
   int dev = 0;
@@ -474,7 +478,7 @@ cudaError_t launch_roll_t(const Launch& L_, const void* fin, void* fout, int pul
 // Opt-in shared memory, and the persistent grid: SMs x resident CTAs per SM.
 template <class S, bool LOOK, bool INFLOW, bool KEEP>
 cudaError_t prepare_roll_t(int dev, int sms) {
-  using C = RollCfg<S, LOOK>;
+  using C = RollCfg<S, LOOK, KEEP>;
   using G = RollGeom<S, LOOK, C::XW, C::RR>;
   cudaError_t e = cudaFuncSetAttribute(k_roll<S, LOOK, C::XW, C::RR, INFLOW, KEEP>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_bytes);
@@ -523,7 +527,10 @@ long long roll_ctas(const KParams& p) {
     cudaGetLastError();
     return 4096;
   }
-  constexpr int nt = RollGeom<float, false, RollCfg<float, false>::XW, RollCfg<float, false>::RR>::NT;
+  // the smallest CTA of any strip configuration
+  constexpr int nt32 = RollGeom<float, false, RollCfg<float, false>::XW, RollCfg<float, false>::RR>::NT;
+  constexpr int nt64 = RollGeom<double, false, RollCfg<double, false>::XW, RollCfg<double, false>::RR>::NT;
+  constexpr int nt = nt32 < nt64 ? nt32 : nt64;
   return (long long)sms * ((thr + nt - 1) / nt);
 }
 
